@@ -1,0 +1,438 @@
+"""Benchmark: Fast-SSC decode throughput and frame latency on one node.
+
+Default workload: the (32768, 29492) polar code (Bhattacharyya construction at
+4.0 dB), BPSK-AWGN at 4.0 dB, 4096 frames per step per GPU, float32 LLRs.
+A step is one decode of the batch (every operation of the Fast-SSC list, the
+channel-LLR load and the packed-bit store), one kernel launch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|i8]
+                    [--impl reference] [--workload NAME]
+
+Prints one JSON line (rank 0). With --impl reference the CPU oracle is timed on
+the host cores instead (the slow, plain reference of the method).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1504_00353_gb300 import synth  # noqa: E402
+
+METRIC = "info-bit Gbps"
+# Paper numbers for this exact code (Table 3 int8 unrolled decoder, Table 2 float
+# unrolled decoder; Intel i7-4770S, one core): context, other hardware.
+PAPER_GBPS = {("n32768_k29492_4.0db", "i8"): 1.131, ("n32768_k29492_4.0db", "f32"): 0.3151}
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--dtype", choices=["f32", "i8"], default="f32")
+    p.add_argument("--workload", default="n32768_k29492_4.0db", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--batch", type=int, default=0, help="frames per step per GPU (0: workload's)")
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--latency-frames", type=int, default=200)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world,
+                                device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_inputs(wl, batch, seed, dtype):
+    """Info bits, codewords (library's host encoder) and channel LLRs (host)."""
+    from paper_1504_00353_gb300 import polar
+    N, K = wl["N"], wl["K"]
+    mask = synth.frozen_mask(N, K, wl["design_db"])
+    code = polar.polar_code_create(N, K, mask)
+    rng = np.random.default_rng(seed)
+    d = synth.info_bits(rng, batch, K)
+    cw = synth.unpack_bits(polar.polar_encode_systematic(code, synth.pack_bits(d)), N)
+    llr = synth.awgn_llr(rng, cw, wl["ebn0_db"], K / N)
+    if dtype == "i8":
+        llr = synth.quantize_i8(llr)
+    return mask, code, d, llr
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline inputs
+
+def profile_traffic(workload, dtype):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken on
+    the current kernel source (its sha256 prefix is recorded beside the number)."""
+    path = os.path.join(ROOT, "profiles", f"fastssc_decode_{dtype}_{workload}.md")
+    src = os.path.join(ROOT, "paper_1504_00353_gb300", "csrc", "polar_kernels.cu")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if not cur.startswith(h.group(1)):
+        return None
+    return float(m.group(1))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+
+def time_oracle(mask, llr, budget_cpu_s=12.0, threads=None):
+    """Oracle Fast-SSC over a bounded sample, frames split across host threads
+    (the C loop runs without the GIL). Returns (frames, seconds, threads)."""
+    import oracle
+    oracle.build()
+    n_total = llr.shape[0]
+    t0 = time.perf_counter()
+    oracle.decode_batch(mask, llr[:1])
+    per = max(time.perf_counter() - t0, 1e-6)
+    T = threads or min(os.cpu_count() or 1, 16)
+    frames = int(max(T, min(n_total, budget_cpu_s / per)))
+    frames = max(T, frames - frames % T)
+    frames = min(frames, n_total - n_total % T if n_total >= T else n_total)
+    chunks = np.array_split(np.arange(frames), T)
+    errs = []
+
+    def work(ix):
+        try:
+            oracle.decode_batch(mask, llr, frames=ix)
+        except Exception as e:  # pragma: no cover
+            errs.append(e)
+
+    ths = [threading.Thread(target=work, args=(c,)) for c in chunks if len(c)]
+    t0 = time.perf_counter()
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    if errs:
+        raise errs[0]
+    return frames, dt, len(ths)
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = dict(synth.WORKLOADS[args.workload])
+    N, K = wl["N"], wl["K"]
+    batch = args.batch or wl["n_frames"]
+    sample = min(batch, 256)
+    # The oracle only needs the LLRs; build them without the GPU library.
+    import oracle
+    oracle.build()
+    mask = synth.frozen_mask(N, K, wl["design_db"])
+    rng = np.random.default_rng(wl["seed"])
+    d = synth.info_bits(rng, sample, K)
+    cw = np.stack([oracle.encode_systematic(mask, r) for r in d])
+    llr = synth.awgn_llr(rng, cw, wl["ebn0_db"], K / N)
+    if args.dtype == "i8":
+        llr = synth.quantize_i8(llr)
+    for _ in range(args.warmup):
+        time_oracle(mask, llr[: min(sample, 16)], budget_cpu_s=0.5)
+    tot_frames, tot_s, T = 0, 0.0, 1
+    for _ in range(args.steps):
+        f, s, T = time_oracle(mask, llr, budget_cpu_s=max(2.0, 60.0 / max(args.steps, 1)))
+        tot_frames += f
+        tot_s += s
+    gbps = K * tot_frames / tot_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbps, "unit": "Gbps",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "K": K, "batch": batch,
+                   "ebn0_db": wl["ebn0_db"], "parallelism": "frames split across host threads"},
+        "cpu_baseline": {"value": gbps, "unit": "Gbps", "cores": T, "kind": "oracle",
+                         "sample": f"{tot_frames} frames of {args.workload} over {args.steps} "
+                                   f"steps, plain C Fast-SSC oracle, {T} host threads"},
+        "e2e": {"value": gbps, "unit": "Gbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, world, rank, local):
+    import torch
+
+    from paper_1504_00353_gb300 import polar
+
+    wl = dict(synth.WORKLOADS[args.workload])
+    N, K = wl["N"], wl["K"]
+    batch = args.batch or wl["n_frames"]
+    i8 = args.dtype == "i8"
+    es = 1 if i8 else 4
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    mask, code, d, llr = make_inputs(wl, batch, wl["seed"] + 1000 * rank, args.dtype)
+    decode = polar.polar_decode_i8 if i8 else polar.polar_decode
+    in_bytes = batch * N * es
+    # Enough distinct input buffers that successive steps never find their
+    # input in L2 (each step streams more than L2 before a buffer is reused).
+    n_buf = 1 if in_bytes > 2 * L2_BYTES else int(np.ceil(3 * L2_BYTES / in_bytes)) + 1
+    base = torch.from_numpy(llr).to(dev)
+    bufs = [base] + [base[torch.randperm(batch, generator=torch.Generator().manual_seed(i))
+                          .to(dev)].contiguous() for i in range(1, n_buf)]
+    out = torch.empty((batch, (K + 7) // 8), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # correctness gate against the known transmitted bits (not a parity test)
+    decode(code, bufs[0], out)
+    torch.cuda.synchronize()
+    polar.polar_code_check(code)
+    fer = float((out.cpu().numpy() != synth.pack_bits(d)).any(axis=1).mean())
+
+    for i in range(args.warmup):
+        decode(code, bufs[i % n_buf], out)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            decode(code, bufs[i % n_buf], out)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    polar.polar_code_check(code)
+    elapsed_ms = max_over_ranks(world, t_start.elapsed_time(t_end))
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    value = world * batch * K * args.steps / (elapsed_ms * 1e-3) / 1e9
+
+    # end to end: pinned host LLRs -> device -> decode -> packed bits back to host,
+    # chunked over two streams so copies overlap decoding
+    host_in = torch.from_numpy(llr).pin_memory()
+    host_out = torch.empty((batch, (K + 7) // 8), dtype=torch.uint8).pin_memory()
+    chunks = 4
+    cs = (batch + chunks - 1) // chunks
+    streams = [torch.cuda.Stream(dev) for _ in range(2)]
+    dbuf = torch.empty_like(base)
+
+    def e2e_step():
+        for c in range(chunks):
+            s = streams[c % 2]
+            lo, hi = c * cs, min(batch, (c + 1) * cs)
+            with torch.cuda.stream(s):
+                dbuf[lo:hi].copy_(host_in[lo:hi], non_blocking=True)
+                decode(code, dbuf[lo:hi], out[lo:hi], stream=s)
+                host_out[lo:hi].copy_(out[lo:hi], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_gbps = world * batch * K * e2e_steps / e2e_s / 1e9
+
+    # batch-1 frame latency (device, and with the frame's copies)
+    lat_dev, lat_e2e = [], []
+    nlat = min(args.latency_frames, batch)
+    one_in = torch.empty((1, N), dtype=base.dtype, device=dev)
+    one_out = torch.empty((1, (K + 7) // 8), dtype=torch.uint8, device=dev)
+    h1 = torch.empty((1, (K + 7) // 8), dtype=torch.uint8).pin_memory()
+    for f in range(nlat + 5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        one_in.copy_(bufs[0][f % batch: f % batch + 1])
+        torch.cuda.synchronize()
+        a.record(stream)
+        decode(code, one_in, one_out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_in.copy_(host_in[f % batch: f % batch + 1], non_blocking=True)
+        decode(code, one_in, one_out)
+        h1.copy_(one_out, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if f >= 5:
+            lat_dev.append(a.elapsed_time(b) * 1e3)
+            lat_e2e.append((t1 - t0) * 1e6)
+
+    hbm_peak, peak_kind = peaks()
+    alg_bytes = batch * (N * es + (K + 7) // 8)
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = profile_traffic(args.workload, args.dtype)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gbps", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / PAPER_GBPS[(args.workload, args.dtype)]
+                        if (args.workload, args.dtype) in PAPER_GBPS else None),
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "K": K, "global_batch": batch * world,
+                   "batch_per_gpu": batch, "ebn0_db": wl["ebn0_db"], "llr": args.dtype,
+                   "parallelism": f"frames sharded over {world} GPU(s), no collective",
+                   "l2": (f"{n_buf} distinct input buffers of {in_bytes / 2**20:.0f} MiB "
+                          "rotated; inputs larger than L2"),
+                   "launch": polar.polar_code_get_launch(code, i8, batch),
+                   "fer_check": fer},
+        "latency_us": {"batch": 1, "frames": nlat,
+                       "device_p50": float(np.percentile(lat_dev, 50)),
+                       "device_p99": float(np.percentile(lat_dev, 99)),
+                       "e2e_p50": float(np.percentile(lat_e2e, 50)),
+                       "e2e_p99": float(np.percentile(lat_e2e, 99))},
+        "e2e": {"value": e2e_gbps, "unit": "Gbps",
+                "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
+                "d2h_bytes_per_step": int(host_out.numel())},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": launch_ms},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        f, s, T = time_oracle(mask, llr)
+        line["cpu_baseline"] = {"value": K * f / s / 1e9, "unit": "Gbps", "cores": T,
+                                "kind": "oracle",
+                                "sample": f"{f} frames of {args.workload} ({args.dtype}), "
+                                          f"plain C Fast-SSC oracle, {T} host threads, "
+                                          f"{s:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the CPU oracle arm: rank 0 alone runs and prints, other ranks exit
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_reference(args, 1, 0)
+        return
+    world, rank, local = dist_init(args)
+    run_native(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * polar_gb300.h - C ABI of the GB300 (sm_103a) Fast-SSC decoder for systematic
+ * polar codes.
+ *
+ * Method: Giard, Sarkis, Leroux, Thibeault, Gross, "Low-Latency Software Polar
+ * Decoders" (arXiv 1504.00353). The decoder walks the code's Fast-SSC tree
+ * depth first (Sec. II-C/II-D): min-sum F (Eq. 1), G (Eq. 2) and G_0R, the XOR
+ * Combine (Eq. 3) and Combine_0R, and the Rate-0, Rate-1 (Eq. 4),
+ * Repetition and SPC constituent decoders, on float32 or saturating int8 LLRs.
+ *
+ * Conventions shared by every call:
+ *  - natural bit order (Sec. II-A, G_N = F_2^{(x)log2 N}, no bit reversal);
+ *  - frozen_mask[i] = 1 marks a frozen bit-channel, 0 an information one;
+ *    the information set A is used in increasing index order;
+ *  - BPSK maps bit 0 to +1, so an LLR >= 0 decides bit 0 (Eq. 4);
+ *  - packed bits are LSB first: bit k is byte k/8, bit position k%8; the unused
+ *    high bits of a row's last byte are written as 0;
+ *  - LLR and bit arrays are frame-major: frame f of an [n][N] LLR array starts
+ *    at element f*N, frame f of the output at byte f*ceil(K/8).
+ *
+ * Threading: a polar_code_t is immutable after creation (its per-device tables
+ * are filled once, under a lock) and may be used from several host threads and
+ * streams at once. Every decode call is asynchronous on the stream it is given.
+ *
+ * Errors: calls return polar_status. Argument and launch errors are reported
+ * synchronously; a device-side wait that ran out of time is recorded in the
+ * code's status word and reported by polar_code_check(). No call aborts the
+ * process.
+ */
+#ifndef POLAR_GB300_H
+#define POLAR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct polar_code polar_code_t;
+
+/* A CUDA stream handle (the same type as cudaStream_t); NULL is the legacy
+ * default stream. */
+typedef struct CUstream_st *polar_stream_t;
+
+typedef enum {
+    POLAR_OK = 0,
+    POLAR_EINVAL = -1,   /* bad N, K, mask, handle, size or configuration */
+    POLAR_ENOMEM = -2,   /* host or device allocation failed */
+    POLAR_ECUDA = -3,    /* a CUDA runtime call failed (no device, launch error) */
+    POLAR_EALIGN = -4,   /* an LLR pointer is not 16-byte aligned */
+    POLAR_ETIMEOUT = -5  /* a bounded device-side wait expired (see polar_code_check) */
+} polar_status;
+
+/* Text for a status code (static storage, never NULL). */
+const char *polar_status_str(polar_status s);
+
+/* Create a code handle for an (N, K) polar code (Sec. II-A: the N-K frozen
+ * bit-channels are fixed to zero).
+ *   N           power of two, 2 <= N <= 2^20.
+ *   K           number of information bits; must equal the number of zeros
+ *               in frozen_mask, 0 <= K <= N.
+ *   frozen_mask host array of N bytes, 1 = frozen, 0 = information; copied.
+ *   out         receives the handle; untouched on error.
+ * The host builds the depth-first Fast-SSC operation list (Listing 1 is this
+ * list for the (8,5) code of Fig. 2a) and the tables that pack the decoded
+ * information bits. When a CUDA device is present the tables are also copied
+ * to the current device; other devices are filled on their first decode.
+ * Returns POLAR_EINVAL for a bad N, K or mask, POLAR_ENOMEM on allocation
+ * failure, POLAR_ECUDA if the upload to a present device fails. */
+polar_status polar_code_create(uint32_t N, uint32_t K, const uint8_t *frozen_mask,
+                               polar_code_t **out);
+
+/* As polar_code_create, with the largest Repetition and SPC node sizes the
+ * decoder may use (Sec. II-D). A larger node of that type is split into its
+ * two children instead. 0 disables the node type; UINT32_MAX (the default of
+ * polar_code_create) leaves it unlimited. Setting max_spc = 0 gives the
+ * node set of the paper's GPU decoder (Sec. V: SPC nodes not used). */
+polar_status polar_code_create_ex(uint32_t N, uint32_t K, const uint8_t *frozen_mask,
+                                  uint32_t max_rep, uint32_t max_spc,
+                                  polar_code_t **out);
+
+/* Release a handle and its device tables. Synchronises with nothing: the
+ * caller must ensure no decode that uses the handle is still running.
+ * NULL is accepted. */
+void polar_code_destroy(polar_code_t *code);
+
+/* N, K and the length of the operation list. Any pointer may be NULL. */
+polar_status polar_code_info(const polar_code_t *code, uint32_t *N, uint32_t *K,
+                             uint32_t *n_ops);
+
+/* Copy the operation list (depth-first order, Listing 1) to host arrays of
+ * `capacity` entries: kind[i] (0 F, 1 G, 2 G_0R, 3 Combine, 4 Combine_0R,
+ * 5 Rate-0 fill of a right child, 6 Rate-1/Info, 7 Repetition, 8 SPC),
+ * nv[i] = node size N_v, off[i] = index of the node's first leaf.
+ * *n_ops receives the list length. POLAR_EINVAL if capacity is too small. */
+polar_status polar_code_schedule(const polar_code_t *code, uint32_t *kind, uint32_t *nv,
+                                 uint32_t *off, size_t capacity, size_t *n_ops);
+
+/* Systematic encoding on the host (the paper decodes codewords but does not
+ * describe the encoder; this is the two-step encoder x = ((d on A) G)|_A G).
+ *   info_packed     host, n_frames rows of ceil(K/8) bytes, packed LSB first.
+ *   codeword_packed host, n_frames rows of ceil(N/8) bytes, packed LSB first.
+ * Returns POLAR_EINVAL if the frozen set is not one for which the two-step
+ * encoder is systematic (x restricted to A must equal the data). */
+polar_status polar_encode_systematic(const polar_code_t *code, const uint8_t *info_packed,
+                                     uint8_t *codeword_packed, size_t n_frames);
+
+/* Fast-SSC decode of n_frames frames of float32 channel LLRs (Sec. II-D).
+ *   llr       device, [n_frames][N] float32, 16-byte aligned; read only.
+ *   bits_out  device, [n_frames][ceil(K/8)] bytes: the estimated codeword
+ *             restricted to A (= the information bits of a systematic code),
+ *             packed LSB first.
+ *   stream    CUDA stream; the call is asynchronous on it.
+ * n_frames = 0 (or K = 0 with nothing to write) is a no-op returning POLAR_OK.
+ * Arithmetic: F is an exact min and sign, G one IEEE binary32 add, the
+ * Repetition sum folds t[i] + t[i+m] for m = N_v/2, ..., 1 (the order SC
+ * uses), SPC flips the lowest index of least |LLR|; results are bit-exact
+ * with a scalar CPU evaluation in that order. Device scratch, when the code
+ * needs it, is taken with cudaMallocAsync on `stream` and returned on it.
+ * Returns POLAR_EALIGN for a misaligned llr, POLAR_EINVAL for NULL pointers,
+ * POLAR_ECUDA when no device is present or the launch fails. */
+polar_status polar_decode(const polar_code_t *code, const float *llr, uint8_t *bits_out,
+                          size_t n_frames, polar_stream_t stream);
+
+/* As polar_decode for int8 LLRs in [-127, 127] (-128 must not occur). G and
+ * the Repetition sums saturate to [-127, 127] (Sec. III-A: saturating adders;
+ * Listing 4: saturating add then max(-127)). */
+polar_status polar_decode_i8(const polar_code_t *code, const int8_t *llr,
+                             uint8_t *bits_out, size_t n_frames, polar_stream_t stream);
+
+/* Number of float values one frame writes to a trace (the summed N_v/2 of
+ * every F, G and G_0R operation). */
+size_t polar_code_trace_len(const polar_code_t *code);
+
+/* Test/debug decode that also records, for every frame and in list order, the
+ * N_v/2 output LLRs of each F, G and G_0R operation into
+ *   alpha_trace  device, [n_frames][polar_code_trace_len()] float32
+ *                (int8 decodes store their integer values as floats).
+ * llr is float32 when is_i8 = 0 and int8 when is_i8 = 1. Same kernel code
+ * path as the plain decode, with the trace stores added. */
+polar_status polar_decode_trace(const polar_code_t *code, const void *llr, int is_i8,
+                                uint8_t *bits_out, float *alpha_trace, size_t n_frames,
+                                polar_stream_t stream);
+
+/* Launch shape for one LLR type (is_i8 = 0 float32, 1 int8). 0 in any field
+ * restores the automatic choice for that field.
+ *   threads          threads per CTA (one CTA decodes one frame at a time),
+ *                    multiple of 32, <= 1024.
+ *   smem_stage_max   largest alpha stage (node size) kept in shared memory;
+ *                    power of two >= 64. Wider stages live in per-CTA device
+ *                    scratch.
+ *   warp_stage_max   operations on nodes of size <= this run on one warp
+ *                    without CTA barriers; power of two >= 2.
+ *   ctas_per_sm      resident CTAs per SM for the persistent grid.
+ *   stage_channel    1: copy each frame's LLRs into shared memory with a bulk
+ *                    async copy (double buffered), 2: read them from device
+ *                    memory in place, 0: automatic.
+ * Not thread-safe against concurrent decodes of the same handle. */
+polar_status polar_code_set_launch(polar_code_t *code, int is_i8, uint32_t threads,
+                                   uint32_t smem_stage_max, uint32_t warp_stage_max,
+                                   uint32_t ctas_per_sm, uint32_t stage_channel);
+
+/* The launch shape a decode of n_frames frames would use now (after the
+ * automatic choices), written to the non-NULL pointers. smem_bytes is the
+ * dynamic shared memory per CTA, grid the number of CTAs, scratch_bytes the
+ * device scratch the call allocates. */
+polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n_frames,
+                                   uint32_t *threads, uint32_t *smem_stage_max,
+                                   uint32_t *warp_stage_max, uint32_t *ctas_per_sm,
+                                   uint32_t *stage_channel, uint32_t *grid,
+                                   size_t *smem_bytes, size_t *scratch_bytes);
+
+/* Wait for `stream`, then read and clear the handle's device status word on
+ * the current device. POLAR_ETIMEOUT if a bounded device wait expired since
+ * the last check, POLAR_OK otherwise. */
+polar_status polar_code_check(polar_code_t *code, polar_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLAR_GB300_H */

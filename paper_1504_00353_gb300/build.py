@@ -1,0 +1,52 @@
+"""Compile libpolar_gb300.so in place (nvcc, sm_103a only).
+
+    python -m paper_1504_00353_gb300.build
+
+One shared library holds the host code (handles, operation-list compiler,
+encoder, launch selection, the C ABI) and the CUDA kernels. Floating point is
+strict IEEE: no --use_fast_math, so F/G/Repetition match a scalar evaluation.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libpolar_gb300.so")
+SOURCES = [os.path.join(CSRC, "polar_host.cpp"), os.path.join(CSRC, "polar_kernels.cu")]
+HEADERS = [os.path.join(CSRC, "polar_internal.h"), os.path.join(ROOT, "include", "polar_gb300.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in SOURCES + HEADERS)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not _stale():
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc(), "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
+           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-o", tmp, *SOURCES]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,598 @@
+// Host side of libpolar_gb300: code handles, the Fast-SSC operation-list
+// compiler, output-packing tables, the systematic encoder, launch-shape
+// selection and the C ABI entry points declared in include/polar_gb300.h.
+//
+// Method: Giard et al., "Low-Latency Software Polar Decoders" (arXiv 1504.00353).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "polar_gb300.h"
+#include "polar_internal.h"
+
+using namespace polar;
+
+namespace {
+
+constexpr uint32_t kMaxN = 1u << 20;
+constexpr size_t kMaxDevices = 64;
+
+enum NodeType { NT_R0, NT_R1, NT_REP, NT_SPC, NT_SPLIT };
+
+struct DeviceState {
+    bool ready = false;
+    int *status = nullptr;
+    uint32_t *ext = nullptr;  // ext_mask | ext_pre | ext_wstart
+    std::map<uint32_t, DevOp *> ops_by_w;
+};
+
+struct UserLaunch {
+    uint32_t threads = 0, smem_stage_max = 0, warp_stage_max = 0, ctas_per_sm = 0,
+             stage_channel = 0;
+};
+
+int log2u(uint32_t v) {
+    int l = 0;
+    while ((1u << l) < v) ++l;
+    return l;
+}
+
+bool is_pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+}  // namespace
+
+struct polar_code {
+    uint32_t N = 0, K = 0, log2N = 0, max_rep = UINT32_MAX, max_spc = UINT32_MAX;
+    std::vector<uint8_t> frozen;
+    std::vector<uint32_t> frozen_prefix;  // frozen count in [0, i)
+    std::vector<uint32_t> info_idx;       // A in increasing order
+    std::vector<HostOp> ops;
+    std::vector<uint32_t> trace_off;      // per op (F/G/G_0R), floats
+    size_t trace_len = 0;
+    uint32_t NW = 1, KW = 0;
+    std::vector<uint32_t> ext_mask, ext_pre, ext_wstart;
+    UserLaunch user[2];
+    std::mutex mu;
+    // One slot per device ordinal, sized once so pointers into it stay valid.
+    std::vector<DeviceState> dev = std::vector<DeviceState>(kMaxDevices);
+
+    // ---------------------------------------------------------- classification
+    // Node type from its leaves, in this order: all frozen -> Rate-0, none
+    // frozen -> Rate-1, only the last leaf information -> Repetition, only the
+    // first leaf frozen -> SPC (Sec. II-D), otherwise split. A size-2 node
+    // [frozen, info] is therefore a Repetition node.
+    NodeType classify(uint32_t off, uint32_t n) const {
+        const uint32_t nf = frozen_prefix[off + n] - frozen_prefix[off];
+        if (nf == n) return NT_R0;
+        if (nf == 0) return NT_R1;
+        if (nf == n - 1 && !frozen[off + n - 1] && n <= max_rep) return NT_REP;
+        if (nf == 1 && frozen[off] && n <= max_spc) return NT_SPC;
+        return NT_SPLIT;
+    }
+
+    void emit(uint32_t kind, uint32_t n, uint32_t off) {
+        ops.push_back(HostOp{kind, static_cast<uint32_t>(log2u(n)), off});
+    }
+
+    // Depth-first operation list of Listing 1: a node with a Rate-0 left child
+    // is G_0R, right subtree, Combine_0R; otherwise F, left subtree, then
+    // either a Rate-0 fill of the right half (no G, Combine leaves beta_l as is)
+    // or G, right subtree, Combine.
+    void compile(uint32_t off, uint32_t n) {
+        switch (classify(off, n)) {
+        case NT_R0: emit(OP_R0, n, off); return;
+        case NT_R1: emit(OP_R1, n, off); return;
+        case NT_REP: emit(OP_REP, n, off); return;
+        case NT_SPC: emit(OP_SPC, n, off); return;
+        default: break;
+        }
+        const uint32_t h = n / 2;
+        if (classify(off, h) == NT_R0) {
+            emit(OP_G0R, n, off);
+            compile(off + h, h);
+            emit(OP_C0R, n, off);
+            return;
+        }
+        emit(OP_F, n, off);
+        compile(off, h);
+        if (classify(off + h, h) == NT_R0) {
+            emit(OP_R0, h, off + h);
+            return;
+        }
+        emit(OP_G, n, off);
+        compile(off + h, h);
+        emit(OP_C, n, off);
+    }
+
+    void build_tables() {
+        frozen_prefix.assign(N + 1, 0);
+        for (uint32_t i = 0; i < N; ++i) frozen_prefix[i + 1] = frozen_prefix[i] + frozen[i];
+        info_idx.clear();
+        for (uint32_t i = 0; i < N; ++i)
+            if (!frozen[i]) info_idx.push_back(i);
+        ops.clear();
+        compile(0, N);
+        trace_off.assign(ops.size(), 0);
+        size_t t = 0;
+        for (size_t i = 0; i < ops.size(); ++i) {
+            trace_off[i] = static_cast<uint32_t>(t);
+            if (ops[i].kind <= OP_G0R) t += size_t(1) << (ops[i].log2n - 1);
+        }
+        trace_len = t;
+        // Output packing: beta word w holds leaves [32w, 32w+32).
+        NW = N >= 32 ? N / 32 : 1;
+        KW = (K + 31) / 32;
+        ext_mask.assign(NW, 0);
+        ext_pre.assign(NW, 0);
+        for (uint32_t i = 0; i < N; ++i)
+            if (!frozen[i]) ext_mask[i >> 5] |= 1u << (i & 31);
+        uint32_t pre = 0;
+        for (uint32_t w = 0; w < NW; ++w) {
+            ext_pre[w] = pre;
+            pre += static_cast<uint32_t>(__builtin_popcount(ext_mask[w]));
+        }
+        ext_wstart.assign(KW, 0);
+        uint32_t w = 0;
+        for (uint32_t u = 0; u < KW; ++u) {
+            const uint32_t lo = 32 * u;
+            while (w < NW && ext_pre[w] + static_cast<uint32_t>(__builtin_popcount(ext_mask[w])) <= lo)
+                ++w;
+            ext_wstart[u] = w;
+        }
+    }
+
+    std::vector<DevOp> device_ops(uint32_t W) const {
+        std::vector<DevOp> d(ops.size());
+        uint32_t next = static_cast<uint32_t>(ops.size());
+        for (size_t r = ops.size(); r-- > 0;) {
+            const HostOp &o = ops[r];
+            const bool warp = (1u << o.log2n) <= W;
+            if (!warp) next = static_cast<uint32_t>(r);
+            d[r].meta = o.kind | (o.log2n << 8) | (warp ? OPF_WARP : 0u);
+            d[r].off = o.off;
+            d[r].next = warp ? next : 0u;
+            d[r].trace_off = trace_off[r];
+        }
+        return d;
+    }
+
+    ~polar_code() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        for (size_t d = 0; d < dev.size(); ++d) {
+            DeviceState &s = dev[d];
+            if (!s.ready) continue;
+            if (cudaSetDevice(static_cast<int>(d)) != cudaSuccess) continue;
+            cudaFree(s.status);
+            cudaFree(s.ext);
+            for (auto &kv : s.ops_by_w) cudaFree(kv.second);
+        }
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+};
+
+namespace {
+
+// Make sure the current device holds the code's tables (and the op list for W).
+polar_status ensure_device(polar_code *c, int device, uint32_t W, DeviceState **out,
+                           const DevOp **ops_out = nullptr) {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (device < 0 || static_cast<size_t>(device) >= c->dev.size()) return POLAR_ECUDA;
+    DeviceState &s = c->dev[device];
+    if (!s.ready) {
+        if (cudaMalloc(&s.status, sizeof(int)) != cudaSuccess) return POLAR_ENOMEM;
+        if (cudaMemset(s.status, 0, sizeof(int)) != cudaSuccess) return POLAR_ECUDA;
+        const size_t n = size_t(c->NW) * 2 + c->KW;
+        if (cudaMalloc(&s.ext, std::max<size_t>(n, 1) * 4) != cudaSuccess) {
+            cudaFree(s.status);
+            return POLAR_ENOMEM;
+        }
+        std::vector<uint32_t> h(std::max<size_t>(n, 1), 0);
+        std::copy(c->ext_mask.begin(), c->ext_mask.end(), h.begin());
+        std::copy(c->ext_pre.begin(), c->ext_pre.end(), h.begin() + c->NW);
+        std::copy(c->ext_wstart.begin(), c->ext_wstart.end(), h.begin() + 2 * c->NW);
+        if (cudaMemcpy(s.ext, h.data(), h.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return POLAR_ECUDA;
+        s.ready = true;
+    }
+    if (!s.ops_by_w.count(W)) {
+        std::vector<DevOp> d = c->device_ops(W);
+        DevOp *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(d.size(), 1) * sizeof(DevOp)) != cudaSuccess)
+            return POLAR_ENOMEM;
+        if (!d.empty() &&
+            cudaMemcpy(p, d.data(), d.size() * sizeof(DevOp), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(p);
+            return POLAR_ECUDA;
+        }
+        s.ops_by_w[W] = p;
+    }
+    if (ops_out) *ops_out = s.ops_by_w[W];
+    *out = &s;
+    return POLAR_OK;
+}
+
+struct DeviceProps {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+
+DeviceProps device_props(int device) {
+    static std::mutex mu;
+    static std::map<int, DeviceProps> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(device);
+    if (it != cache.end()) return it->second;
+    DeviceProps p;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) == cudaSuccess) p.sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) == cudaSuccess)
+        p.smem_optin = static_cast<size_t>(v);
+    cache[device] = p;
+    return p;
+}
+
+uint32_t pow2_floor(uint32_t v) {
+    uint32_t p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// Launch shape for a decode of n_frames frames on `device`.
+polar_status choose_shape(const polar_code *c, bool is_i8, size_t n_frames, int device,
+                          LaunchShape *sh) {
+    const DeviceProps dp = device_props(device);
+    if (dp.sms <= 0 || dp.smem_optin == 0) return POLAR_ECUDA;
+    const UserLaunch &u = c->user[is_i8 ? 1 : 0];
+    const uint32_t es = is_i8 ? 1 : 4;
+    const uint32_t N = c->N;
+    const bool latency = n_frames * 2 <= static_cast<size_t>(dp.sms);
+
+    uint32_t T = u.threads;
+    if (!T) {
+        if (latency) T = N >= 8192 ? 1024 : std::max<uint32_t>(64, pow2_floor(std::max<uint32_t>(N / 8, 32)));
+        else T = N <= 2048 ? 128 : (N <= 8192 ? 256 : 512);
+    }
+    T = std::min<uint32_t>(std::max<uint32_t>(T, 32), 1024);
+
+    const bool can_stage = (size_t(N) * es) % 16 == 0;
+    const size_t budget = latency ? dp.smem_optin : std::min<size_t>(dp.smem_optin, 112 * 1024);
+    uint32_t S = u.smem_stage_max ? std::max<uint32_t>(u.smem_stage_max, 64) : 0;
+    if (!S) {
+        S = std::max<uint32_t>(N / 2, 1);
+        while (S > 64 && kernel_smem_bytes(N, S, T, is_i8, false) > budget) S /= 2;
+    }
+    S = std::min<uint32_t>(S, std::max<uint32_t>(N / 2, 1));
+    uint32_t stage = 0;
+    if (u.stage_channel == 1) stage = can_stage ? 1 : 0;
+    else if (u.stage_channel == 2) stage = 0;
+    else stage = (can_stage && kernel_smem_bytes(N, S, T, is_i8, true) <= budget) ? 1 : 0;
+    // Too little SMEM for the chosen shape: fall back to smaller stages.
+    while (kernel_smem_bytes(N, S, T, is_i8, stage) > dp.smem_optin && S > 64) S /= 2;
+    if (kernel_smem_bytes(N, S, T, is_i8, stage) > dp.smem_optin) {
+        if (stage) stage = 0;
+        if (kernel_smem_bytes(N, S, T, is_i8, stage) > dp.smem_optin) return POLAR_EINVAL;
+    }
+    const uint32_t W = u.warp_stage_max ? u.warp_stage_max : 128;
+    const size_t smem = kernel_smem_bytes(N, S, T, is_i8, stage);
+    int occ = kernel_max_ctas_per_sm(is_i8, stage, T, smem);
+    if (occ <= 0) return POLAR_EINVAL;
+    uint32_t cps = u.ctas_per_sm ? std::min<uint32_t>(u.ctas_per_sm, static_cast<uint32_t>(occ))
+                                 : static_cast<uint32_t>(occ);
+    const size_t grid = std::min<size_t>(n_frames, size_t(dp.sms) * cps);
+    sh->threads = T;
+    sh->smem_stage_max = S;
+    sh->warp_stage_max = W;
+    sh->ctas_per_sm = cps;
+    sh->stage_channel = stage;
+    sh->grid = static_cast<uint32_t>(std::max<size_t>(grid, 1));
+    sh->smem_bytes = smem;
+    const size_t g = (N / 2 > S) ? size_t(N) - 2 * size_t(S) : 0;
+    sh->scratch_elems_per_cta = g ? ((g * es + 15) / 16 * 16) / es : 0;
+    return POLAR_OK;
+}
+
+polar_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return POLAR_OK;
+    if (e == cudaErrorMemoryAllocation) return POLAR_ENOMEM;
+    return POLAR_ECUDA;
+}
+
+polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
+                         uint8_t *bits_out, float *trace, size_t n_frames,
+                         polar_stream_t stream) {
+    if (!code) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!llr || (!bits_out && code->K > 0)) return POLAR_EINVAL;
+    if (reinterpret_cast<uintptr_t>(llr) % 16 != 0) return POLAR_EALIGN;
+    if (trace && code->trace_len == 0 && code->K == 0) return POLAR_OK;
+    if (code->K == 0 && !trace) return POLAR_OK;  // nothing to write
+    polar_code *c = const_cast<polar_code *>(code);
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    LaunchShape sh{};
+    polar_status st = choose_shape(c, is_i8, n_frames, device, &sh);
+    if (st != POLAR_OK) return st;
+    DeviceState *ds = nullptr;
+    const DevOp *dops = nullptr;
+    st = ensure_device(c, device, sh.warp_stage_max, &ds, &dops);
+    if (st != POLAR_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    KernelArgs a{};
+    a.ops = dops;
+    a.ext_mask = ds->ext;
+    a.ext_pre = ds->ext + c->NW;
+    a.ext_wstart = ds->ext + 2 * c->NW;
+    a.status = ds->status;
+    a.llr = llr;
+    a.out = bits_out;
+    a.trace = trace;
+    a.n_frames = n_frames;
+    a.trace_stride = c->trace_len;
+    a.gstride = sh.scratch_elems_per_cta;
+    a.n_ops = static_cast<uint32_t>(c->ops.size());
+    a.N = c->N;
+    a.log2N = c->log2N;
+    a.K = c->K;
+    a.S = sh.smem_stage_max;
+    a.NW = c->NW;
+    a.KW = c->KW;
+    a.out_row = (c->K + 7) / 8;
+
+    void *scratch = nullptr;
+    const size_t scratch_bytes = size_t(sh.grid) * sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
+    if (scratch_bytes) {
+        cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+    }
+    a.gscratch = scratch;
+    cudaError_t e = launch_decode(is_i8, trace != nullptr, sh.stage_channel != 0, sh, a, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    return POLAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *polar_status_str(polar_status s) {
+    switch (s) {
+    case POLAR_OK: return "ok";
+    case POLAR_EINVAL: return "invalid argument";
+    case POLAR_ENOMEM: return "out of memory";
+    case POLAR_ECUDA: return "CUDA error";
+    case POLAR_EALIGN: return "LLR pointer not 16-byte aligned";
+    case POLAR_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+polar_status polar_code_create_ex(uint32_t N, uint32_t K, const uint8_t *frozen_mask,
+                                  uint32_t max_rep, uint32_t max_spc, polar_code_t **out) {
+    if (!out || !frozen_mask) return POLAR_EINVAL;
+    if (N < 2 || N > kMaxN || !is_pow2(N) || K > N) return POLAR_EINVAL;
+    uint32_t zeros = 0;
+    for (uint32_t i = 0; i < N; ++i) {
+        if (frozen_mask[i] > 1) return POLAR_EINVAL;
+        zeros += frozen_mask[i] == 0;
+    }
+    if (zeros != K) return POLAR_EINVAL;
+    polar_code *c = new (std::nothrow) polar_code;
+    if (!c) return POLAR_ENOMEM;
+    try {
+        c->N = N;
+        c->K = K;
+        c->log2N = static_cast<uint32_t>(log2u(N));
+        c->max_rep = max_rep;
+        c->max_spc = max_spc;
+        c->frozen.assign(frozen_mask, frozen_mask + N);
+        c->build_tables();
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return POLAR_ENOMEM;
+    }
+    // Upload to the current device when one is present.
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+        int device = 0;
+        DeviceState *ds = nullptr;
+        if (cudaGetDevice(&device) != cudaSuccess) {
+            delete c;
+            return POLAR_ECUDA;
+        }
+        polar_status st = ensure_device(c, device, 128, &ds);
+        if (st != POLAR_OK) {
+            delete c;
+            return st;
+        }
+    } else {
+        cudaGetLastError();
+    }
+    *out = c;
+    return POLAR_OK;
+}
+
+polar_status polar_code_create(uint32_t N, uint32_t K, const uint8_t *frozen_mask,
+                               polar_code_t **out) {
+    return polar_code_create_ex(N, K, frozen_mask, UINT32_MAX, UINT32_MAX, out);
+}
+
+void polar_code_destroy(polar_code_t *code) { delete code; }
+
+polar_status polar_code_info(const polar_code_t *code, uint32_t *N, uint32_t *K,
+                             uint32_t *n_ops) {
+    if (!code) return POLAR_EINVAL;
+    if (N) *N = code->N;
+    if (K) *K = code->K;
+    if (n_ops) *n_ops = static_cast<uint32_t>(code->ops.size());
+    return POLAR_OK;
+}
+
+polar_status polar_code_schedule(const polar_code_t *code, uint32_t *kind, uint32_t *nv,
+                                 uint32_t *off, size_t capacity, size_t *n_ops) {
+    if (!code) return POLAR_EINVAL;
+    if (n_ops) *n_ops = code->ops.size();
+    if (capacity < code->ops.size()) return POLAR_EINVAL;
+    for (size_t i = 0; i < code->ops.size(); ++i) {
+        if (kind) kind[i] = code->ops[i].kind;
+        if (nv) nv[i] = 1u << code->ops[i].log2n;
+        if (off) off[i] = code->ops[i].off;
+    }
+    return POLAR_OK;
+}
+
+size_t polar_code_trace_len(const polar_code_t *code) { return code ? code->trace_len : 0; }
+
+// x = u F^{(x)n} on 64-bit words, bit i of the frame = bit (i % 64) of word i/64.
+static void transform_words(uint64_t *w, uint32_t N) {
+    static const uint64_t kMask[6] = {0x5555555555555555ull, 0x3333333333333333ull,
+                                      0x0F0F0F0F0F0F0F0Full, 0x00FF00FF00FF00FFull,
+                                      0x0000FFFF0000FFFFull, 0x00000000FFFFFFFFull};
+    const uint32_t nw = N >= 64 ? N / 64 : 1;
+    for (uint32_t h = 1, l = 0; h < 64 && h < N; h *= 2, ++l)
+        for (uint32_t j = 0; j < nw; ++j) w[j] ^= (w[j] >> h) & kMask[l];
+    for (uint32_t hw = 1; hw < nw; hw *= 2)
+        for (uint32_t b = 0; b < nw; b += 2 * hw)
+            for (uint32_t j = b; j < b + hw; ++j) w[j] ^= w[j + hw];
+}
+
+polar_status polar_encode_systematic(const polar_code_t *code, const uint8_t *info_packed,
+                                     uint8_t *codeword_packed, size_t n_frames) {
+    if (!code) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if ((!info_packed && code->K) || !codeword_packed) return POLAR_EINVAL;
+    const uint32_t N = code->N, K = code->K;
+    const uint32_t nw = N >= 64 ? N / 64 : 1;
+    const size_t in_row = (K + 7) / 8, out_row = (N + 7) / 8;
+    std::vector<uint64_t> info_words(nw, 0), w(nw);
+    for (uint32_t i : code->info_idx) info_words[i >> 6] |= 1ull << (i & 63);
+    for (size_t f = 0; f < n_frames; ++f) {
+        const uint8_t *d = info_packed + f * in_row;
+        std::fill(w.begin(), w.end(), 0ull);
+        for (uint32_t k = 0; k < K; ++k)
+            if ((d[k >> 3] >> (k & 7)) & 1u) {
+                const uint32_t i = code->info_idx[k];
+                w[i >> 6] |= 1ull << (i & 63);
+            }
+        transform_words(w.data(), N);
+        for (uint32_t j = 0; j < nw; ++j) w[j] &= info_words[j];
+        transform_words(w.data(), N);
+        for (uint32_t k = 0; k < K; ++k) {
+            const uint32_t i = code->info_idx[k];
+            if (((w[i >> 6] >> (i & 63)) & 1ull) != ((d[k >> 3] >> (k & 7)) & 1u))
+                return POLAR_EINVAL;
+        }
+        uint8_t *x = codeword_packed + f * out_row;
+        for (size_t b = 0; b < out_row; ++b)
+            x[b] = static_cast<uint8_t>((w[b >> 3] >> (8 * (b & 7))) & 0xFFu);
+        if (N < 8) x[0] &= static_cast<uint8_t>((1u << N) - 1u);
+    }
+    return POLAR_OK;
+}
+
+polar_status polar_decode(const polar_code_t *code, const float *llr, uint8_t *bits_out,
+                          size_t n_frames, polar_stream_t stream) {
+    return decode_impl(code, llr, false, bits_out, nullptr, n_frames, stream);
+}
+
+polar_status polar_decode_i8(const polar_code_t *code, const int8_t *llr, uint8_t *bits_out,
+                             size_t n_frames, polar_stream_t stream) {
+    return decode_impl(code, llr, true, bits_out, nullptr, n_frames, stream);
+}
+
+polar_status polar_decode_trace(const polar_code_t *code, const void *llr, int is_i8,
+                                uint8_t *bits_out, float *alpha_trace, size_t n_frames,
+                                polar_stream_t stream) {
+    if (!code || (!alpha_trace && code->trace_len)) return POLAR_EINVAL;
+    if (code->trace_len == 0 || !alpha_trace) {
+        return decode_impl(code, llr, is_i8 != 0, bits_out, nullptr, n_frames, stream);
+    }
+    return decode_impl(code, llr, is_i8 != 0, bits_out, alpha_trace, n_frames, stream);
+}
+
+polar_status polar_code_set_launch(polar_code_t *code, int is_i8, uint32_t threads,
+                                   uint32_t smem_stage_max, uint32_t warp_stage_max,
+                                   uint32_t ctas_per_sm, uint32_t stage_channel) {
+    if (!code) return POLAR_EINVAL;
+    if (threads && (threads % 32 || threads > 1024)) return POLAR_EINVAL;
+    if (smem_stage_max && (!is_pow2(smem_stage_max) || smem_stage_max < 64)) return POLAR_EINVAL;
+    if (warp_stage_max && (!is_pow2(warp_stage_max) || warp_stage_max < 2)) return POLAR_EINVAL;
+    if (stage_channel > 2) return POLAR_EINVAL;
+    UserLaunch &u = code->user[is_i8 ? 1 : 0];
+    u.threads = threads;
+    u.smem_stage_max = smem_stage_max;
+    u.warp_stage_max = warp_stage_max;
+    u.ctas_per_sm = ctas_per_sm;
+    u.stage_channel = stage_channel;
+    return POLAR_OK;
+}
+
+polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n_frames,
+                                   uint32_t *threads, uint32_t *smem_stage_max,
+                                   uint32_t *warp_stage_max, uint32_t *ctas_per_sm,
+                                   uint32_t *stage_channel, uint32_t *grid, size_t *smem_bytes,
+                                   size_t *scratch_bytes) {
+    if (!code) return POLAR_EINVAL;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    LaunchShape sh{};
+    polar_status st = choose_shape(code, is_i8 != 0, std::max<size_t>(n_frames, 1), device, &sh);
+    if (st != POLAR_OK) return st;
+    if (threads) *threads = sh.threads;
+    if (smem_stage_max) *smem_stage_max = sh.smem_stage_max;
+    if (warp_stage_max) *warp_stage_max = sh.warp_stage_max;
+    if (ctas_per_sm) *ctas_per_sm = sh.ctas_per_sm;
+    if (stage_channel) *stage_channel = sh.stage_channel;
+    if (grid) *grid = sh.grid;
+    if (smem_bytes) *smem_bytes = sh.smem_bytes;
+    if (scratch_bytes) *scratch_bytes = size_t(sh.grid) * sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
+    return POLAR_OK;
+}
+
+polar_status polar_code_check(polar_code_t *code, polar_stream_t stream) {
+    if (!code) return POLAR_EINVAL;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    std::lock_guard<std::mutex> g(code->mu);
+    if (static_cast<size_t>(device) >= code->dev.size() || !code->dev[device].ready) return POLAR_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, code->dev[device].status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return POLAR_ECUDA;
+    if (v) {
+        cudaMemset(code->dev[device].status, 0, sizeof(int));
+        return POLAR_ETIMEOUT;
+    }
+    return POLAR_OK;
+}
+
+}  // extern "C"

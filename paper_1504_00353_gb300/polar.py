@@ -1,0 +1,245 @@
+"""Python binding of libpolar_gb300 (include/polar_gb300.h), same names as the C ABI.
+
+Argument marshalling only: torch tensors become device pointers, torch streams
+become cudaStream_t handles, numpy arrays become host pointers. Every step of
+the decode runs in the library's CUDA kernels; there is no CPU or PyTorch
+fallback, and importing this module raises if the library is not built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+UNLIMITED = 0xFFFFFFFF
+OP_NAMES = ["F", "G", "G_0R", "Combine", "Combine_0R", "R0", "Info", "Rep", "SPC"]
+STATUS = {0: "POLAR_OK", -1: "POLAR_EINVAL", -2: "POLAR_ENOMEM", -3: "POLAR_ECUDA",
+          -4: "POLAR_EALIGN", -5: "POLAR_ETIMEOUT"}
+
+# Every symbol include/polar_gb300.h declares.
+EXPORTS = [
+    "polar_status_str", "polar_code_create", "polar_code_create_ex", "polar_code_destroy",
+    "polar_code_info", "polar_code_schedule", "polar_encode_systematic", "polar_decode",
+    "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
+    "polar_code_get_launch", "polar_code_check",
+]
+
+
+class PolarError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} "
+                         f"({_lib.polar_status_str(status).decode()})")
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_1504_00353_gb300.build` (or __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, u8p, u32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint32)
+    u32, sz, st = ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    sig = {
+        "polar_status_str": ([st], ctypes.c_char_p),
+        "polar_code_create": ([u32, u32, u8p, ctypes.POINTER(vp)], st),
+        "polar_code_create_ex": ([u32, u32, u8p, u32, u32, ctypes.POINTER(vp)], st),
+        "polar_code_destroy": ([vp], None),
+        "polar_code_info": ([vp, u32p, u32p, u32p], st),
+        "polar_code_schedule": ([vp, u32p, u32p, u32p, sz, szp], st),
+        "polar_encode_systematic": ([vp, u8p, u8p, sz], st),
+        "polar_decode": ([vp, vp, vp, sz, vp], st),
+        "polar_decode_i8": ([vp, vp, vp, sz, vp], st),
+        "polar_code_trace_len": ([vp], sz),
+        "polar_decode_trace": ([vp, vp, st, vp, vp, sz, vp], st),
+        "polar_code_set_launch": ([vp, st, u32, u32, u32, u32, u32], st),
+        "polar_code_get_launch": ([vp, st, sz, u32p, u32p, u32p, u32p, u32p, u32p, szp, szp], st),
+        "polar_code_check": ([vp, vp], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise PolarError(status, what)
+
+
+class PolarCode:
+    """Owns a polar_code_t handle (destroyed with the object)."""
+
+    def __init__(self, handle: int, N: int, K: int, frozen: np.ndarray):
+        self.handle = ctypes.c_void_p(handle)
+        self.N, self.K = N, K
+        self.frozen = frozen
+        self.out_row = (K + 7) // 8
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.polar_code_destroy(h)
+            self.handle = ctypes.c_void_p(0)
+
+
+def polar_code_create(N: int, K: int, frozen_mask, max_rep: int | None = None,
+                      max_spc: int | None = None) -> PolarCode:
+    m = np.ascontiguousarray(np.asarray(frozen_mask, dtype=np.uint8))
+    if m.size != N:
+        raise ValueError("frozen_mask must have N entries")
+    h = ctypes.c_void_p()
+    p = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    if max_rep is None and max_spc is None:
+        _check(_lib.polar_code_create(N, K, p, ctypes.byref(h)), "polar_code_create")
+    else:
+        _check(_lib.polar_code_create_ex(N, K, p, UNLIMITED if max_rep is None else max_rep,
+                                         UNLIMITED if max_spc is None else max_spc,
+                                         ctypes.byref(h)), "polar_code_create_ex")
+    return PolarCode(h.value, N, K, m.copy())
+
+
+def polar_code_destroy(code: PolarCode):
+    code.__del__()
+
+
+def polar_code_info(code: PolarCode):
+    N, K, n = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(_lib.polar_code_info(code.handle, ctypes.byref(N), ctypes.byref(K), ctypes.byref(n)),
+           "polar_code_info")
+    return N.value, K.value, n.value
+
+
+def polar_code_schedule(code: PolarCode):
+    """[(name, N_v, offset)] in depth-first order."""
+    n = polar_code_info(code)[2]
+    kind = np.zeros(max(n, 1), np.uint32)
+    nv = np.zeros(max(n, 1), np.uint32)
+    off = np.zeros(max(n, 1), np.uint32)
+    cnt = ctypes.c_size_t()
+    P = ctypes.POINTER(ctypes.c_uint32)
+    _check(_lib.polar_code_schedule(code.handle, kind.ctypes.data_as(P), nv.ctypes.data_as(P),
+                                    off.ctypes.data_as(P), kind.size, ctypes.byref(cnt)),
+           "polar_code_schedule")
+    return [(OP_NAMES[kind[i]], int(nv[i]), int(off[i])) for i in range(cnt.value)]
+
+
+def polar_code_trace_len(code: PolarCode) -> int:
+    return int(_lib.polar_code_trace_len(code.handle))
+
+
+def polar_encode_systematic(code: PolarCode, info_packed) -> np.ndarray:
+    """Host systematic encoder: info_packed uint8[n, ceil(K/8)] -> uint8[n, ceil(N/8)]."""
+    d = np.ascontiguousarray(np.asarray(info_packed, dtype=np.uint8))
+    d = d.reshape(-1, code.out_row) if code.out_row else d.reshape(-1, 0)
+    n = d.shape[0]
+    x = np.zeros((n, (code.N + 7) // 8), np.uint8)
+    P = ctypes.POINTER(ctypes.c_uint8)
+    src = d.ctypes.data_as(P) if d.size else P()
+    _check(_lib.polar_encode_systematic(code.handle, src, x.ctypes.data_as(P), n),
+           "polar_encode_systematic")
+    return x
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _out_tensor(code, llr, bits_out, n):
+    import torch
+    if bits_out is None:
+        bits_out = torch.empty((n, code.out_row), dtype=torch.uint8, device=llr.device)
+    if bits_out.dtype != torch.uint8 or not bits_out.is_contiguous() or bits_out.numel() < n * code.out_row:
+        raise ValueError("bits_out must be a contiguous uint8 tensor of n*ceil(K/8) bytes")
+    return bits_out
+
+
+def _decode(fn, name, code, llr, bits_out, n_frames, stream, dtype):
+    import torch
+    if not isinstance(llr, torch.Tensor) or not llr.is_cuda:
+        raise TypeError(f"{name}: llr must be a CUDA tensor")
+    if llr.dtype != dtype or not llr.is_contiguous():
+        raise TypeError(f"{name}: llr must be a contiguous {dtype} tensor")
+    n = llr.numel() // code.N if n_frames is None else int(n_frames)
+    if n * code.N > llr.numel():
+        raise ValueError(f"{name}: llr holds fewer than n_frames*N values")
+    bits_out = _out_tensor(code, llr, bits_out, n)
+    _check(fn(code.handle, ctypes.c_void_p(llr.data_ptr()), ctypes.c_void_p(bits_out.data_ptr()),
+              n, _stream_handle(stream)), name)
+    return bits_out
+
+
+def polar_decode(code: PolarCode, llr, bits_out=None, n_frames=None, stream=None):
+    """Decode float32 LLRs [n, N] (CUDA tensor) into packed info bits [n, ceil(K/8)]."""
+    import torch
+    return _decode(_lib.polar_decode, "polar_decode", code, llr, bits_out, n_frames, stream,
+                   torch.float32)
+
+
+def polar_decode_i8(code: PolarCode, llr, bits_out=None, n_frames=None, stream=None):
+    """Decode int8 LLRs in [-127, 127] [n, N] (CUDA tensor)."""
+    import torch
+    return _decode(_lib.polar_decode_i8, "polar_decode_i8", code, llr, bits_out, n_frames,
+                   stream, torch.int8)
+
+
+def polar_decode_trace(code: PolarCode, llr, bits_out=None, trace=None, stream=None):
+    """Decode and record every F/G/G_0R output; returns (bits_out, trace[n, trace_len])."""
+    import torch
+    if not llr.is_cuda or not llr.is_contiguous() or llr.dtype not in (torch.float32, torch.int8):
+        raise TypeError("llr must be a contiguous CUDA float32 or int8 tensor")
+    n = llr.numel() // code.N
+    bits_out = _out_tensor(code, llr, bits_out, n)
+    tl = polar_code_trace_len(code)
+    if trace is None:
+        trace = torch.empty((n, tl), dtype=torch.float32, device=llr.device)
+    _check(_lib.polar_decode_trace(code.handle, ctypes.c_void_p(llr.data_ptr()),
+                                   1 if llr.dtype == torch.int8 else 0,
+                                   ctypes.c_void_p(bits_out.data_ptr()),
+                                   ctypes.c_void_p(trace.data_ptr()), n, _stream_handle(stream)),
+           "polar_decode_trace")
+    return bits_out, trace
+
+
+def polar_code_set_launch(code: PolarCode, is_i8: bool, threads=0, smem_stage_max=0,
+                          warp_stage_max=0, ctas_per_sm=0, stage_channel=0):
+    _check(_lib.polar_code_set_launch(code.handle, int(bool(is_i8)), threads, smem_stage_max,
+                                      warp_stage_max, ctas_per_sm, stage_channel),
+           "polar_code_set_launch")
+
+
+def polar_code_get_launch(code: PolarCode, is_i8: bool, n_frames: int) -> dict:
+    v = [ctypes.c_uint32() for _ in range(6)]
+    s = [ctypes.c_size_t() for _ in range(2)]
+    _check(_lib.polar_code_get_launch(code.handle, int(bool(is_i8)), n_frames,
+                                      *[ctypes.byref(x) for x in v], *[ctypes.byref(x) for x in s]),
+           "polar_code_get_launch")
+    keys = ["threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm", "stage_channel", "grid"]
+    d = {k: x.value for k, x in zip(keys, v)}
+    d["smem_bytes"], d["scratch_bytes"] = s[0].value, s[1].value
+    return d
+
+
+def polar_code_check(code: PolarCode, stream=None):
+    _check(_lib.polar_code_check(code.handle, _stream_handle(stream)), "polar_code_check")
+
+
+def polar_status_str(status: int) -> str:
+    return _lib.polar_status_str(status).decode()
