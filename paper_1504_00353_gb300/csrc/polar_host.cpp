@@ -13,6 +13,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "polar_gb300.h"
@@ -30,8 +31,7 @@ enum NodeType { NT_R0, NT_R1, NT_REP, NT_SPC, NT_SPLIT };
 struct DeviceState {
     bool ready = false;
     int *status = nullptr;
-    uint32_t *ext = nullptr;  // ext_mask | ext_pre | ext_wstart
-    std::map<uint32_t, DevOp *> ops_by_w;
+    uint32_t *tables = nullptr;  // ops | trace_offs | ext_mask | ext_pre | ext_wstart
 };
 
 struct UserLaunch {
@@ -79,7 +79,21 @@ struct polar_code {
     }
 
     void emit(uint32_t kind, uint32_t n, uint32_t off) {
-        ops.push_back(HostOp{kind, static_cast<uint32_t>(log2u(n)), off});
+        ops.push_back(HostOp{kind, static_cast<uint32_t>(log2u(n)), off, 0u});
+    }
+
+    // A node of at most kRegSubtree leaves whose parent is larger (or the root)
+    // starts a subtree that one warp decodes in registers: mark its ops.
+    void compile_top(uint32_t off, uint32_t n) {
+        if (n > kRegSubtree) {
+            compile(off, n);
+            return;
+        }
+        const size_t first = ops.size();
+        compile(off, n);
+        for (size_t i = first; i < ops.size(); ++i) ops[i].flags |= OPW_REG;
+        ops[first].flags |= OPW_REG_ENTER;
+        ops.back().flags |= OPW_REG_EXIT;
     }
 
     // Depth-first operation list of Listing 1: a node with a Rate-0 left child
@@ -95,20 +109,21 @@ struct polar_code {
         default: break;
         }
         const uint32_t h = n / 2;
+        const bool top = n > kRegSubtree;  // children may start register subtrees
         if (classify(off, h) == NT_R0) {
             emit(OP_G0R, n, off);
-            compile(off + h, h);
+            top ? compile_top(off + h, h) : compile(off + h, h);
             emit(OP_C0R, n, off);
             return;
         }
         emit(OP_F, n, off);
-        compile(off, h);
+        top ? compile_top(off, h) : compile(off, h);
         if (classify(off + h, h) == NT_R0) {
             emit(OP_R0, h, off + h);
             return;
         }
         emit(OP_G, n, off);
-        compile(off + h, h);
+        top ? compile_top(off + h, h) : compile(off + h, h);
         emit(OP_C, n, off);
     }
 
@@ -119,7 +134,7 @@ struct polar_code {
         for (uint32_t i = 0; i < N; ++i)
             if (!frozen[i]) info_idx.push_back(i);
         ops.clear();
-        compile(0, N);
+        compile_top(0, N);
         trace_off.assign(ops.size(), 0);
         size_t t = 0;
         for (size_t i = 0; i < ops.size(); ++i) {
@@ -149,17 +164,12 @@ struct polar_code {
         }
     }
 
-    std::vector<DevOp> device_ops(uint32_t W) const {
-        std::vector<DevOp> d(ops.size());
-        uint32_t next = static_cast<uint32_t>(ops.size());
-        for (size_t r = ops.size(); r-- > 0;) {
+    // Packed operation words (see polar_internal.h).
+    std::vector<uint32_t> device_ops() const {
+        std::vector<uint32_t> d(ops.size());
+        for (size_t r = 0; r < ops.size(); ++r) {
             const HostOp &o = ops[r];
-            const bool warp = (1u << o.log2n) <= W;
-            if (!warp) next = static_cast<uint32_t>(r);
-            d[r].meta = o.kind | (o.log2n << 8) | (warp ? OPF_WARP : 0u);
-            d[r].off = o.off;
-            d[r].next = warp ? next : 0u;
-            d[r].trace_off = trace_off[r];
+            d[r] = o.kind | (o.log2n << 4) | o.flags | ((o.off >> o.log2n) << 12);
         }
         return d;
     }
@@ -172,8 +182,7 @@ struct polar_code {
             if (!s.ready) continue;
             if (cudaSetDevice(static_cast<int>(d)) != cudaSuccess) continue;
             cudaFree(s.status);
-            cudaFree(s.ext);
-            for (auto &kv : s.ops_by_w) cudaFree(kv.second);
+            cudaFree(s.tables);
         }
         if (cur >= 0) cudaSetDevice(cur);
     }
@@ -181,41 +190,37 @@ struct polar_code {
 
 namespace {
 
-// Make sure the current device holds the code's tables (and the op list for W).
-polar_status ensure_device(polar_code *c, int device, uint32_t W, DeviceState **out,
-                           const DevOp **ops_out = nullptr) {
+// Make sure `device` holds the code's tables (uploaded once, under the lock).
+polar_status ensure_device(polar_code *c, int device, DeviceState **out) {
     std::lock_guard<std::mutex> g(c->mu);
     if (device < 0 || static_cast<size_t>(device) >= c->dev.size()) return POLAR_ECUDA;
     DeviceState &s = c->dev[device];
     if (!s.ready) {
+        const size_t nops = c->ops.size();
+        const size_t n = 2 * nops + size_t(c->NW) * 2 + c->KW;
+        std::vector<uint32_t> h(std::max<size_t>(n, 1), 0);
+        const std::vector<uint32_t> d = c->device_ops();
+        std::copy(d.begin(), d.end(), h.begin());
+        std::copy(c->trace_off.begin(), c->trace_off.end(), h.begin() + nops);
+        std::copy(c->ext_mask.begin(), c->ext_mask.end(), h.begin() + 2 * nops);
+        std::copy(c->ext_pre.begin(), c->ext_pre.end(), h.begin() + 2 * nops + c->NW);
+        std::copy(c->ext_wstart.begin(), c->ext_wstart.end(), h.begin() + 2 * nops + 2 * c->NW);
         if (cudaMalloc(&s.status, sizeof(int)) != cudaSuccess) return POLAR_ENOMEM;
-        if (cudaMemset(s.status, 0, sizeof(int)) != cudaSuccess) return POLAR_ECUDA;
-        const size_t n = size_t(c->NW) * 2 + c->KW;
-        if (cudaMalloc(&s.ext, std::max<size_t>(n, 1) * 4) != cudaSuccess) {
+        if (cudaMalloc(&s.tables, h.size() * 4) != cudaSuccess) {
             cudaFree(s.status);
+            s.status = nullptr;
             return POLAR_ENOMEM;
         }
-        std::vector<uint32_t> h(std::max<size_t>(n, 1), 0);
-        std::copy(c->ext_mask.begin(), c->ext_mask.end(), h.begin());
-        std::copy(c->ext_pre.begin(), c->ext_pre.end(), h.begin() + c->NW);
-        std::copy(c->ext_wstart.begin(), c->ext_wstart.end(), h.begin() + 2 * c->NW);
-        if (cudaMemcpy(s.ext, h.data(), h.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemset(s.status, 0, sizeof(int)) != cudaSuccess ||
+            cudaMemcpy(s.tables, h.data(), h.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(s.status);
+            cudaFree(s.tables);
+            s.status = nullptr;
+            s.tables = nullptr;
             return POLAR_ECUDA;
+        }
         s.ready = true;
     }
-    if (!s.ops_by_w.count(W)) {
-        std::vector<DevOp> d = c->device_ops(W);
-        DevOp *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(d.size(), 1) * sizeof(DevOp)) != cudaSuccess)
-            return POLAR_ENOMEM;
-        if (!d.empty() &&
-            cudaMemcpy(p, d.data(), d.size() * sizeof(DevOp), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaFree(p);
-            return POLAR_ECUDA;
-        }
-        s.ops_by_w[W] = p;
-    }
-    if (ops_out) *ops_out = s.ops_by_w[W];
     *out = &s;
     return POLAR_OK;
 }
@@ -238,6 +243,22 @@ DeviceProps device_props(int device) {
         p.smem_optin = static_cast<size_t>(v);
     cache[device] = p;
     return p;
+}
+
+// Resident CTAs per SM for a kernel variant and shape, cached per device.
+int occupancy(int device, bool is_i8, bool stage, uint32_t T, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, bool, bool, uint32_t, size_t>, int> cache;
+    const auto key = std::make_tuple(device, is_i8, stage, T, smem);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const int n = kernel_max_ctas_per_sm(is_i8, stage, T, smem);
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = n;
+    return n;
 }
 
 uint32_t pow2_floor(uint32_t v) {
@@ -281,9 +302,9 @@ polar_status choose_shape(const polar_code *c, bool is_i8, size_t n_frames, int 
         if (stage) stage = 0;
         if (kernel_smem_bytes(N, S, T, is_i8, stage) > dp.smem_optin) return POLAR_EINVAL;
     }
-    const uint32_t W = u.warp_stage_max ? u.warp_stage_max : 128;
+    const uint32_t W = std::max<uint32_t>(u.warp_stage_max ? u.warp_stage_max : 512, kRegSubtree);
     const size_t smem = kernel_smem_bytes(N, S, T, is_i8, stage);
-    int occ = kernel_max_ctas_per_sm(is_i8, stage, T, smem);
+    int occ = occupancy(device, is_i8, stage != 0, T, smem);
     if (occ <= 0) return POLAR_EINVAL;
     uint32_t cps = u.ctas_per_sm ? std::min<uint32_t>(u.ctas_per_sm, static_cast<uint32_t>(occ))
                                  : static_cast<uint32_t>(occ);
@@ -325,16 +346,17 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     polar_status st = choose_shape(c, is_i8, n_frames, device, &sh);
     if (st != POLAR_OK) return st;
     DeviceState *ds = nullptr;
-    const DevOp *dops = nullptr;
-    st = ensure_device(c, device, sh.warp_stage_max, &ds, &dops);
+    st = ensure_device(c, device, &ds);
     if (st != POLAR_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     KernelArgs a{};
-    a.ops = dops;
-    a.ext_mask = ds->ext;
-    a.ext_pre = ds->ext + c->NW;
-    a.ext_wstart = ds->ext + 2 * c->NW;
+    const size_t nops = c->ops.size();
+    a.ops = ds->tables;
+    a.trace_offs = ds->tables + nops;
+    a.ext_mask = ds->tables + 2 * nops;
+    a.ext_pre = ds->tables + 2 * nops + c->NW;
+    a.ext_wstart = ds->tables + 2 * nops + 2 * c->NW;
     a.status = ds->status;
     a.llr = llr;
     a.out = bits_out;
@@ -347,6 +369,7 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     a.log2N = c->log2N;
     a.K = c->K;
     a.S = sh.smem_stage_max;
+    a.log2W = static_cast<uint32_t>(log2u(sh.warp_stage_max));
     a.NW = c->NW;
     a.KW = c->KW;
     a.out_row = (c->K + 7) / 8;
@@ -419,7 +442,7 @@ polar_status polar_code_create_ex(uint32_t N, uint32_t K, const uint8_t *frozen_
             delete c;
             return POLAR_ECUDA;
         }
-        polar_status st = ensure_device(c, device, 128, &ds);
+        polar_status st = ensure_device(c, device, &ds);
         if (st != POLAR_OK) {
             delete c;
             return st;

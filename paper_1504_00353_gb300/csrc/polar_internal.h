@@ -22,21 +22,30 @@ enum OpKind : uint32_t {
     OP_SPC = 8,   // SPC: hard decisions, flip least-|alpha| bit on odd parity
 };
 
-// Flag bits of DevOp::meta.
+// One operation as the kernel reads it: a 32-bit word
+//   bits 0-3   kind (OpKind)
+//   bits 4-8   log2(N_v)
+//   bit  9     inside a register-resident subtree (N_v <= kRegSubtree)
+//   bit  10    first op of such a subtree: (N_v, off) is the subtree root
+//   bit  11    last op of such a subtree: store its bits to beta
+//   bits 12-31 off >> log2(N_v), off = index of the node's first leaf
+// Whether an op runs on one warp or on the whole CTA is decided at run time
+// from N_v and the launch's warp_stage_max.
 enum : uint32_t {
-    OPF_WARP = 1u << 16,  // executed by warp 0 alone (node size <= warp_stage_max)
+    OPW_REG = 1u << 9,
+    OPW_REG_ENTER = 1u << 10,
+    OPW_REG_EXIT = 1u << 11,
 };
 
-// One operation as the kernel reads it: 16 bytes, one vector load.
-struct alignas(16) DevOp {
-    uint32_t meta;       // kind (bits 0-7) | log2(N_v) (bits 8-15) | flags
-    uint32_t off;        // index of the node's first leaf (its beta offset)
-    uint32_t next;       // for warp ops: index of the first non-warp op after the run
-    uint32_t trace_off;  // F/G/G_0R: offset of the N_v/2 outputs in a frame's trace
-};
+__host__ __device__ inline uint32_t op_kind(uint32_t w) { return w & 0xFu; }
+__host__ __device__ inline uint32_t op_log2n(uint32_t w) { return (w >> 4) & 0x1Fu; }
+__host__ __device__ inline uint32_t op_off(uint32_t w) { return (w >> 12) << op_log2n(w); }
+
+// Largest subtree a warp decodes with its LLRs and bits held in registers.
+constexpr uint32_t kRegSubtree = 32;
 
 struct HostOp {
-    uint32_t kind, log2n, off;
+    uint32_t kind, log2n, off, flags;
 };
 
 // Launch shape of one decode.
@@ -51,17 +60,9 @@ struct LaunchShape {
     size_t scratch_elems_per_cta;  // device alpha scratch per CTA (elements)
 };
 
-// Per-device tables of a code for one warp_stage_max.
-struct DeviceTables {
-    const DevOp *ops;              // n_ops
-    const uint32_t *ext_mask;      // info mask of each beta word (NW words)
-    const uint32_t *ext_pre;       // info bits before beta word w (NW words)
-    const uint32_t *ext_wstart;    // first beta word feeding output word u (KW words)
-    int *status;                   // error flags written by the kernel
-};
-
 struct KernelArgs {
-    const DevOp *ops;
+    const uint32_t *ops;           // n_ops packed operation words
+    const uint32_t *trace_offs;    // per op: offset of its F/G/G_0R outputs in a trace row
     const uint32_t *ext_mask;
     const uint32_t *ext_pre;
     const uint32_t *ext_wstart;
@@ -76,6 +77,7 @@ struct KernelArgs {
     uint32_t n_ops;
     uint32_t N, log2N, K;
     uint32_t S;                // smem_stage_max (already clipped to N/2)
+    uint32_t log2W;            // ops with log2(N_v) <= log2W run on warp 0 alone
     uint32_t NW;               // beta words (max(1, N/32))
     uint32_t KW;               // output 32-bit words (ceil(K/32))
     uint32_t out_row;          // bytes per output row (ceil(K/8))
