@@ -164,12 +164,33 @@ polar_status polar_code_set_launch(polar_code_t *code, int is_i8, uint32_t threa
 /* The launch shape a decode of n_frames frames would use now (after the
  * automatic choices), written to the non-NULL pointers. smem_bytes is the
  * dynamic shared memory per CTA, grid the number of CTAs, scratch_bytes the
- * device scratch the call allocates. */
+ * device scratch the call allocates, unrolled the register-subtree size of the
+ * specialised decoder that will run (0: the operation-list interpreter). */
 polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n_frames,
                                    uint32_t *threads, uint32_t *smem_stage_max,
                                    uint32_t *warp_stage_max, uint32_t *ctas_per_sm,
                                    uint32_t *stage_channel, uint32_t *grid,
-                                   size_t *smem_bytes, size_t *scratch_bytes);
+                                   size_t *smem_bytes, size_t *scratch_bytes,
+                                   uint32_t *unrolled);
+
+/* Build a decoder specialised to this code (Sec. III-B "Unrolled Decoder":
+ * the code's operation list written out with every node size and offset a
+ * compile-time constant), compiled at run time with NVRTC for the current
+ * device, for the launch shape a decode of n_frames frames of this LLR type
+ * uses (is_i8 = 0 float32, 1 int8). Later decodes whose shape matches run it
+ * instead of the operation-list interpreter; results are bit-identical.
+ *   reg_subtree  subtrees of at most this many leaves (power of two, 32..512;
+ *                0 = 256) are decoded entirely in the registers of one warp.
+ * n_frames = 0 releases every specialised decoder of that LLR type.
+ * Blocking; takes seconds for long codes. Call before any stream capture.
+ * Returns POLAR_ECUDA if NVRTC is unavailable or compilation fails (see
+ * polar_code_compile_log); decodes then keep using the interpreter. */
+polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
+                                uint32_t reg_subtree);
+
+/* NVRTC log of the last polar_code_compile on this handle (never NULL; valid
+ * until the next compile or destroy). */
+const char *polar_code_compile_log(const polar_code_t *code);
 
 /* Wait for `stream`, then read and clear the handle's device status word on
  * the current device. POLAR_ETIMEOUT if a bounded device wait expired since

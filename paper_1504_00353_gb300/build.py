@@ -16,8 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpolar_gb300.so")
-SOURCES = [os.path.join(CSRC, "polar_host.cpp"), os.path.join(CSRC, "polar_kernels.cu")]
-HEADERS = [os.path.join(CSRC, "polar_internal.h"), os.path.join(ROOT, "include", "polar_gb300.h")]
+SOURCES = [os.path.join(CSRC, "polar_host.cpp"), os.path.join(CSRC, "polar_codegen.cpp"),
+           os.path.join(CSRC, "polar_kernels.cu")]
+GEN = os.path.join(HERE, "_build")  # generated include: polar_ops.cuh as a C++ string
+HEADERS = [os.path.join(CSRC, "polar_internal.h"), os.path.join(CSRC, "polar_ops.cuh"),
+           os.path.join(ROOT, "include", "polar_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,12 +38,27 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in SOURCES + HEADERS)
 
 
+def _embed_ops_header() -> None:
+    """Write _build/polar_ops_embed.inc: polar_ops.cuh as a raw string literal, the
+    header the run-time (NVRTC) compilation of specialised decoders includes."""
+    os.makedirs(GEN, exist_ok=True)
+    src = open(os.path.join(CSRC, "polar_ops.cuh")).read()
+    assert ")POLAROPS\"" not in src
+    text = 'R"POLAROPS(' + src + ')POLAROPS"\n'
+    path = os.path.join(GEN, "polar_ops_embed.inc")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
+    _embed_ops_header()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
-           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-o", tmp, *SOURCES]
+           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + GEN, "-o", tmp, *SOURCES,
+           "-ldl"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

@@ -1,0 +1,336 @@
+// Decoders specialised to one polar code ("unrolled decoder", Sec. III-B of
+// Giard et al., arXiv 1504.00353): the depth-first Fast-SSC operation list of
+// the code (Listing 1 is this list for the (8,5) code) is written out as CUDA
+// source in which every node size and offset is a compile-time constant, then
+// compiled at run time with NVRTC for the current GPU and loaded with
+// cudaLibraryLoadData.
+//
+// Compared with the operation-list interpreter this removes, per operation,
+// the decode of the op word and the indirect branch to its handler (on one warp
+// these cost several times the operation itself), folds every address and loop
+// bound, and lets subtrees of up to reg_subtree leaves run entirely in
+// registers with statically indexed stages (see polar::RegSub in polar_ops.cuh).
+// Memory-resident operations call the same device functions as the
+// interpreter, with constant arguments.
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <cuda.h>
+#include <nvrtc.h>
+
+#include "polar_internal.h"
+
+namespace polar {
+namespace {
+
+// polar_ops.cuh as a string (generated by the build from the header itself).
+const char kOpsSource[] =
+#include "polar_ops_embed.inc"
+    ;
+
+// NVRTC, resolved at run time so the library loads on machines without it.
+struct Nvrtc {
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    bool ok = false;
+};
+
+const Nvrtc &nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"};
+        void *h = nullptr;
+        for (const char *name : names)
+            if ((h = dlopen(name, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) return;
+        n.create = reinterpret_cast<decltype(n.create)>(dlsym(h, "nvrtcCreateProgram"));
+        n.compile = reinterpret_cast<decltype(n.compile)>(dlsym(h, "nvrtcCompileProgram"));
+        n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+        n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+        n.log_size = reinterpret_cast<decltype(n.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+        n.log = reinterpret_cast<decltype(n.log)>(dlsym(h, "nvrtcGetProgramLog"));
+        n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        n.ok = n.create && n.compile && n.cubin_size && n.cubin && n.log_size && n.log && n.destroy;
+    });
+    return n;
+}
+
+// The driver calls used on compiled decoders, looked up through the runtime
+// (no link dependency on libcuda).
+struct Driver {
+    decltype(&cuKernelGetFunction) kernel_get_function = nullptr;
+    decltype(&cuFuncGetAttribute) func_get_attribute = nullptr;
+    decltype(&cuFuncSetAttribute) func_set_attribute = nullptr;
+    decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) occupancy = nullptr;
+    decltype(&cuLaunchKernel) launch = nullptr;
+    bool ok = false;
+};
+
+const Driver &driver() {
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto get = [](const char *name, void **fp) {
+            cudaDriverEntryPointQueryResult q{};
+            return cudaGetDriverEntryPointByVersion(name, fp, 12000, cudaEnableDefault, &q) ==
+                       cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess && *fp;
+        };
+        d.ok = get("cuKernelGetFunction", reinterpret_cast<void **>(&d.kernel_get_function)) &&
+               get("cuFuncGetAttribute", reinterpret_cast<void **>(&d.func_get_attribute)) &&
+               get("cuFuncSetAttribute", reinterpret_cast<void **>(&d.func_set_attribute)) &&
+               get("cuOccupancyMaxActiveBlocksPerMultiprocessor",
+                   reinterpret_cast<void **>(&d.occupancy)) &&
+               get("cuLaunchKernel", reinterpret_cast<void **>(&d.launch));
+        if (!d.ok) cudaGetLastError();
+    });
+    return d;
+}
+
+// CUfunction of a compiled decoder in the current device's context, with its
+// dynamic shared-memory limit raised to the device maximum (cached per device).
+CUfunction device_function(CompiledKernel *ck) {
+    const Driver &drv = driver();
+    if (!drv.ok) return nullptr;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = ck->func.find(device);
+    if (it != ck->func.end()) return static_cast<CUfunction>(it->second);
+    cudaFree(nullptr);  // make the primary context current
+    CUfunction f = nullptr;
+    if (drv.kernel_get_function(&f, reinterpret_cast<CUkernel>(ck->kernel)) != CUDA_SUCCESS) return nullptr;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (drv.func_set_attribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin) != CUDA_SUCCESS)
+        return nullptr;
+    ck->func[device] = f;
+    return f;
+}
+
+const char *kind_name(uint32_t kind) {
+    static const char *names[] = {"polar::OP_F", "polar::OP_G", "polar::OP_G0R"};
+    return names[kind];
+}
+
+}  // namespace
+
+std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
+                            uint32_t reg_subtree) {
+    const uint32_t N = code.N;
+    const uint32_t S = shape.smem_stage_max;
+    const uint32_t W = shape.warp_stage_max;
+    const std::vector<HostOp> ops = code.build_ops(reg_subtree);
+    const char *T = is_i8 ? "int8_t" : "float";
+
+    std::ostringstream o;
+    o << "// Fast-SSC decoder specialised to one (" << N << ", " << code.K << ") polar code\n"
+      << "#include \"polar_ops.cuh\"\n"
+      << "namespace polar {\n"
+      << "struct GenBody {\n"
+      << "  __device__ __forceinline__ void operator()(const Frame<" << T << "> &fr, float *) const {\n"
+      << "    using T = " << T << ";\n"
+      << "    constexpr uint32_t N = " << N << "u, S = " << S << "u;\n"
+      << "    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;\n"
+      << "    (void)lane; (void)warp;\n";
+
+    auto in = [&](uint32_t n) {
+        std::ostringstream s;
+        s << "gen_in<T, N, S, " << n << "u>(fr)";
+        return s.str();
+    };
+    auto out = [&](uint32_t n) {
+        std::ostringstream s;
+        s << "gen_out<T, S, " << n << "u>(fr)";
+        return s.str();
+    };
+    // Memory-resident operation on the whole CTA or on warp 0.
+    auto mem_op = [&](const HostOp &op, const char *grp) {
+        const uint32_t n = 1u << op.log2n, off = op.off;
+        switch (op.kind) {
+        case OP_F:
+        case OP_G:
+        case OP_G0R:
+            o << "      op_fg<T, " << grp << ", " << kind_name(op.kind) << ">(" << in(n) << ", "
+              << out(n / 2) << ", " << n / 2 << "u, fr.beta, " << off << "u);\n";
+            break;
+        case OP_C:
+        case OP_C0R:
+            o << "      op_combine<" << grp << ">(fr.beta, " << n << "u, " << off << "u, "
+              << (op.kind == OP_C0R ? "true" : "false") << ");\n";
+            break;
+        case OP_R0:
+            o << "      op_r0<" << grp << ">(fr.beta, " << n << "u, " << off << "u);\n";
+            break;
+        case OP_R1:
+            o << "      op_r1<T, " << grp << ">(" << in(n) << ", fr.beta, " << n << "u, " << off
+              << "u);\n";
+            break;
+        case OP_REP:
+            o << "      op_rep<T, " << grp << ">(" << in(n) << ", " << out(n / 2) << ", fr.beta, "
+              << n << "u, " << off << "u);\n";
+            break;
+        default:
+            o << "      op_spc<T, " << grp << ">(" << in(n) << ", fr.beta, " << n << "u, " << off
+              << "u, fr.rkey, fr.rpar);\n";
+            break;
+        }
+    };
+
+    bool in_run = false;
+    uint32_t o0 = 0, n0 = 0;
+    for (size_t i = 0; i < ops.size(); ++i) {
+        const HostOp &op = ops[i];
+        const uint32_t n = 1u << op.log2n;
+        const bool narrow = n <= W || (op.flags & OPW_REG);
+        if (!narrow) {
+            if (in_run) {
+                o << "    }\n    __syncthreads();\n";
+                in_run = false;
+            }
+            o << "    {\n";
+            mem_op(op, "CtaGrp");
+            o << "    }\n    __syncthreads();\n";
+            continue;
+        }
+        if (!in_run) {
+            o << "    if (warp == 0) {\n";
+            in_run = true;
+        }
+        if (!(op.flags & OPW_REG)) {
+            mem_op(op, "WarpGrp");
+            o << "      __syncwarp();\n";
+            continue;
+        }
+        if (op.flags & OPW_REG_ENTER) {
+            o0 = op.off;
+            n0 = n;
+            o << "      {\n        RegSub<T, " << reg_subtree << "u> r;\n        r.lane = lane;\n"
+              << "        r.template enter<" << n0 << "u>(" << in(n0) << ");\n";
+        }
+        const uint32_t p = op.off - o0;
+        o << "        r.template ";
+        switch (op.kind) {
+        case OP_F:
+        case OP_G:
+        case OP_G0R: o << "fg<" << kind_name(op.kind) << ", " << n << "u, " << p << "u>();\n"; break;
+        case OP_C: o << "combine<" << n << "u, " << p << "u, false>();\n"; break;
+        case OP_C0R: o << "combine<" << n << "u, " << p << "u, true>();\n"; break;
+        case OP_R0: o << "r0<" << n << "u, " << p << "u>();\n"; break;
+        case OP_R1: o << "r1<" << n << "u, " << p << "u>();\n"; break;
+        case OP_REP: o << "rep<" << n << "u, " << p << "u>();\n"; break;
+        default: o << "spc<" << n << "u, " << p << "u>();\n"; break;
+        }
+        if (op.flags & OPW_REG_EXIT) {
+            o << "        r.template exit<" << n0 << "u>(fr.beta, " << o0 << "u);\n      }\n"
+              << "      __syncwarp();\n";
+        }
+    }
+    if (in_run) o << "    }\n    __syncthreads();\n";
+    o << "  }\n};\n}  // namespace polar\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << shape.threads << ", "
+      << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n"
+      << "  polar::run_frames<" << T << ", false, " << (shape.stage_channel ? "true" : "false")
+      << ">(a, polar::GenBody{});\n}\n";
+    return o.str();
+}
+
+cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::string *log) {
+    const Nvrtc &nv = nvrtc();
+    if (!nv.ok) {
+        *log = "NVRTC (libnvrtc.so) could not be loaded";
+        return cudaErrorNotSupported;
+    }
+    int device = 0, major = 0, minor = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (e != cudaSuccess) return e;
+    char arch[64];
+    std::snprintf(arch, sizeof arch, "--gpu-architecture=sm_%d%d%s", major, minor, major >= 9 ? "a" : "");
+
+    nvrtcProgram prog = nullptr;
+    const char *hdr_src[] = {kOpsSource};
+    const char *hdr_name[] = {"polar_ops.cuh"};
+    if (nv.create(&prog, src.c_str(), "polar_unrolled.cu", 1, hdr_src, hdr_name) != NVRTC_SUCCESS) {
+        *log = "nvrtcCreateProgram failed";
+        return cudaErrorInvalidValue;
+    }
+    const char *opts[] = {arch, "-std=c++17", "-default-device", "--ptxas-options=-v"};
+    const nvrtcResult r = nv.compile(prog, 4, opts);
+    size_t ls = 0;
+    nv.log_size(prog, &ls);
+    std::string lg(ls, '\0');
+    if (ls) nv.log(prog, &lg[0]);
+    *log = lg;
+    if (r != NVRTC_SUCCESS) {
+        nv.destroy(&prog);
+        return cudaErrorInvalidSource;
+    }
+    size_t cs = 0;
+    nv.cubin_size(prog, &cs);
+    std::vector<char> cubin(cs);
+    nv.cubin(prog, cubin.data());
+    nv.destroy(&prog);
+    e = cudaLibraryLoadData(&out->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaLibraryGetKernel(&out->kernel, out->lib, "polar_unrolled");
+    if (e != cudaSuccess) {
+        cudaLibraryUnload(out->lib);
+        out->lib = nullptr;
+        return e;
+    }
+    CUfunction f = device_function(out);
+    if (!f) {
+        cudaLibraryUnload(out->lib);
+        out->lib = nullptr;
+        *log += "\ncould not obtain the compiled kernel's function handle";
+        return cudaErrorInvalidDeviceFunction;
+    }
+    int regs = 0, local = 0, maxt = 0;
+    driver().func_get_attribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, f);
+    driver().func_get_attribute(&local, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, f);
+    driver().func_get_attribute(&maxt, CU_FUNC_ATTRIBUTE_MAX_THREADS_PER_BLOCK, f);
+    char line[256];
+    std::snprintf(line, sizeof line,
+                  "\nkernel: %d registers, %d bytes local, %d max threads, cubin %zu bytes\n",
+                  regs, local, maxt, cs);
+    *log += line;
+    return cudaSuccess;
+}
+
+int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes) {
+    CUfunction f = device_function(ck);
+    if (!f) return 0;
+    int n = 0;
+    if (driver().occupancy(&n, f, static_cast<int>(threads), smem_bytes) != CUDA_SUCCESS) return 0;
+    return n;
+}
+
+cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const KernelArgs &args,
+                            cudaStream_t stream) {
+    CUfunction f = device_function(ck);
+    if (!f) return cudaErrorInvalidDeviceFunction;
+    void *params[] = {const_cast<KernelArgs *>(&args)};
+    const CUresult r = driver().launch(f, shape.grid, 1, 1, shape.threads, 1, 1,
+                                       static_cast<unsigned>(shape.smem_bytes),
+                                       reinterpret_cast<CUstream>(stream), params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+}  // namespace polar

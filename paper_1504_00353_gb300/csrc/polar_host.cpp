@@ -21,172 +21,21 @@
 
 using namespace polar;
 
-namespace {
-
-constexpr uint32_t kMaxN = 1u << 20;
-constexpr size_t kMaxDevices = 64;
-
-enum NodeType { NT_R0, NT_R1, NT_REP, NT_SPC, NT_SPLIT };
-
-struct DeviceState {
-    bool ready = false;
-    int *status = nullptr;
-    uint32_t *tables = nullptr;  // ops | trace_offs | ext_mask | ext_pre | ext_wstart
-};
-
-struct UserLaunch {
-    uint32_t threads = 0, smem_stage_max = 0, warp_stage_max = 0, ctas_per_sm = 0,
-             stage_channel = 0;
-};
-
-int log2u(uint32_t v) {
-    int l = 0;
-    while ((1u << l) < v) ++l;
-    return l;
+polar_code::~polar_code() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    for (auto &kv : compiled)
+        if (kv.second.lib) cudaLibraryUnload(kv.second.lib);
+    for (size_t d = 0; d < dev.size(); ++d) {
+        DeviceState &s = dev[d];
+        if (!s.ready) continue;
+        if (cudaSetDevice(static_cast<int>(d)) != cudaSuccess) continue;
+        cudaFree(s.status);
+        cudaFree(s.tables);
+    }
+    if (cur >= 0) cudaSetDevice(cur);
 }
 
-bool is_pow2(uint32_t v) { return v && !(v & (v - 1)); }
-
-}  // namespace
-
-struct polar_code {
-    uint32_t N = 0, K = 0, log2N = 0, max_rep = UINT32_MAX, max_spc = UINT32_MAX;
-    std::vector<uint8_t> frozen;
-    std::vector<uint32_t> frozen_prefix;  // frozen count in [0, i)
-    std::vector<uint32_t> info_idx;       // A in increasing order
-    std::vector<HostOp> ops;
-    std::vector<uint32_t> trace_off;      // per op (F/G/G_0R), floats
-    size_t trace_len = 0;
-    uint32_t NW = 1, KW = 0;
-    std::vector<uint32_t> ext_mask, ext_pre, ext_wstart;
-    UserLaunch user[2];
-    std::mutex mu;
-    // One slot per device ordinal, sized once so pointers into it stay valid.
-    std::vector<DeviceState> dev = std::vector<DeviceState>(kMaxDevices);
-
-    // ---------------------------------------------------------- classification
-    // Node type from its leaves, in this order: all frozen -> Rate-0, none
-    // frozen -> Rate-1, only the last leaf information -> Repetition, only the
-    // first leaf frozen -> SPC (Sec. II-D), otherwise split. A size-2 node
-    // [frozen, info] is therefore a Repetition node.
-    NodeType classify(uint32_t off, uint32_t n) const {
-        const uint32_t nf = frozen_prefix[off + n] - frozen_prefix[off];
-        if (nf == n) return NT_R0;
-        if (nf == 0) return NT_R1;
-        if (nf == n - 1 && !frozen[off + n - 1] && n <= max_rep) return NT_REP;
-        if (nf == 1 && frozen[off] && n <= max_spc) return NT_SPC;
-        return NT_SPLIT;
-    }
-
-    void emit(uint32_t kind, uint32_t n, uint32_t off) {
-        ops.push_back(HostOp{kind, static_cast<uint32_t>(log2u(n)), off, 0u});
-    }
-
-    // A node of at most kRegSubtree leaves whose parent is larger (or the root)
-    // starts a subtree that one warp decodes in registers: mark its ops.
-    void compile_top(uint32_t off, uint32_t n) {
-        if (n > kRegSubtree) {
-            compile(off, n);
-            return;
-        }
-        const size_t first = ops.size();
-        compile(off, n);
-        for (size_t i = first; i < ops.size(); ++i) ops[i].flags |= OPW_REG;
-        ops[first].flags |= OPW_REG_ENTER;
-        ops.back().flags |= OPW_REG_EXIT;
-    }
-
-    // Depth-first operation list of Listing 1: a node with a Rate-0 left child
-    // is G_0R, right subtree, Combine_0R; otherwise F, left subtree, then
-    // either a Rate-0 fill of the right half (no G, Combine leaves beta_l as is)
-    // or G, right subtree, Combine.
-    void compile(uint32_t off, uint32_t n) {
-        switch (classify(off, n)) {
-        case NT_R0: emit(OP_R0, n, off); return;
-        case NT_R1: emit(OP_R1, n, off); return;
-        case NT_REP: emit(OP_REP, n, off); return;
-        case NT_SPC: emit(OP_SPC, n, off); return;
-        default: break;
-        }
-        const uint32_t h = n / 2;
-        const bool top = n > kRegSubtree;  // children may start register subtrees
-        if (classify(off, h) == NT_R0) {
-            emit(OP_G0R, n, off);
-            top ? compile_top(off + h, h) : compile(off + h, h);
-            emit(OP_C0R, n, off);
-            return;
-        }
-        emit(OP_F, n, off);
-        top ? compile_top(off, h) : compile(off, h);
-        if (classify(off + h, h) == NT_R0) {
-            emit(OP_R0, h, off + h);
-            return;
-        }
-        emit(OP_G, n, off);
-        top ? compile_top(off + h, h) : compile(off + h, h);
-        emit(OP_C, n, off);
-    }
-
-    void build_tables() {
-        frozen_prefix.assign(N + 1, 0);
-        for (uint32_t i = 0; i < N; ++i) frozen_prefix[i + 1] = frozen_prefix[i] + frozen[i];
-        info_idx.clear();
-        for (uint32_t i = 0; i < N; ++i)
-            if (!frozen[i]) info_idx.push_back(i);
-        ops.clear();
-        compile_top(0, N);
-        trace_off.assign(ops.size(), 0);
-        size_t t = 0;
-        for (size_t i = 0; i < ops.size(); ++i) {
-            trace_off[i] = static_cast<uint32_t>(t);
-            if (ops[i].kind <= OP_G0R) t += size_t(1) << (ops[i].log2n - 1);
-        }
-        trace_len = t;
-        // Output packing: beta word w holds leaves [32w, 32w+32).
-        NW = N >= 32 ? N / 32 : 1;
-        KW = (K + 31) / 32;
-        ext_mask.assign(NW, 0);
-        ext_pre.assign(NW, 0);
-        for (uint32_t i = 0; i < N; ++i)
-            if (!frozen[i]) ext_mask[i >> 5] |= 1u << (i & 31);
-        uint32_t pre = 0;
-        for (uint32_t w = 0; w < NW; ++w) {
-            ext_pre[w] = pre;
-            pre += static_cast<uint32_t>(__builtin_popcount(ext_mask[w]));
-        }
-        ext_wstart.assign(KW, 0);
-        uint32_t w = 0;
-        for (uint32_t u = 0; u < KW; ++u) {
-            const uint32_t lo = 32 * u;
-            while (w < NW && ext_pre[w] + static_cast<uint32_t>(__builtin_popcount(ext_mask[w])) <= lo)
-                ++w;
-            ext_wstart[u] = w;
-        }
-    }
-
-    // Packed operation words (see polar_internal.h).
-    std::vector<uint32_t> device_ops() const {
-        std::vector<uint32_t> d(ops.size());
-        for (size_t r = 0; r < ops.size(); ++r) {
-            const HostOp &o = ops[r];
-            d[r] = o.kind | (o.log2n << 4) | o.flags | ((o.off >> o.log2n) << 12);
-        }
-        return d;
-    }
-
-    ~polar_code() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        for (size_t d = 0; d < dev.size(); ++d) {
-            DeviceState &s = dev[d];
-            if (!s.ready) continue;
-            if (cudaSetDevice(static_cast<int>(d)) != cudaSuccess) continue;
-            cudaFree(s.status);
-            cudaFree(s.tables);
-        }
-        if (cur >= 0) cudaSetDevice(cur);
-    }
-};
 
 namespace {
 
@@ -304,20 +153,50 @@ polar_status choose_shape(const polar_code *c, bool is_i8, size_t n_frames, int 
     }
     const uint32_t W = std::max<uint32_t>(u.warp_stage_max ? u.warp_stage_max : 512, kRegSubtree);
     const size_t smem = kernel_smem_bytes(N, S, T, is_i8, stage);
-    int occ = occupancy(device, is_i8, stage != 0, T, smem);
-    if (occ <= 0) return POLAR_EINVAL;
-    uint32_t cps = u.ctas_per_sm ? std::min<uint32_t>(u.ctas_per_sm, static_cast<uint32_t>(occ))
-                                 : static_cast<uint32_t>(occ);
-    const size_t grid = std::min<size_t>(n_frames, size_t(dp.sms) * cps);
     sh->threads = T;
     sh->smem_stage_max = S;
     sh->warp_stage_max = W;
-    sh->ctas_per_sm = cps;
     sh->stage_channel = stage;
-    sh->grid = static_cast<uint32_t>(std::max<size_t>(grid, 1));
     sh->smem_bytes = smem;
     const size_t g = (N / 2 > S) ? size_t(N) - 2 * size_t(S) : 0;
     sh->scratch_elems_per_cta = g ? ((g * es + 15) / 16 * 16) / es : 0;
+    sh->ctas_per_sm = 0;
+    sh->grid = 0;
+    return POLAR_OK;
+}
+
+// The decoder specialised to this code and shape, if one was compiled.
+CompiledKernel *find_compiled(polar_code *c, bool is_i8, const LaunchShape &sh) {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->compiled.find(CompiledKey{is_i8, sh.threads, sh.smem_stage_max,
+                                           sh.warp_stage_max, sh.stage_channel});
+    return it == c->compiled.end() ? nullptr : &it->second;
+}
+
+int compiled_occupancy(polar_code *c, CompiledKernel *ck, int device, const LaunchShape &sh) {
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        auto it = ck->occupancy.find(device);
+        if (it != ck->occupancy.end()) return it->second;
+    }
+    const int n = compiled_max_ctas(ck, sh.threads, sh.smem_bytes);
+    if (n <= 0) return 0;
+    std::lock_guard<std::mutex> g(c->mu);
+    ck->occupancy[device] = n;
+    return n;
+}
+
+// Fill ctas_per_sm and grid from the resident-CTA count of the kernel used.
+polar_status finish_grid(const polar_code *c, bool is_i8, size_t n_frames, int device, int occ,
+                         LaunchShape *sh) {
+    if (occ <= 0) return POLAR_EINVAL;
+    const DeviceProps dp = device_props(device);
+    const UserLaunch &u = c->user[is_i8 ? 1 : 0];
+    const uint32_t cps = u.ctas_per_sm ? std::min<uint32_t>(u.ctas_per_sm, static_cast<uint32_t>(occ))
+                                       : static_cast<uint32_t>(occ);
+    const size_t grid = std::min<size_t>(n_frames, size_t(dp.sms) * cps);
+    sh->ctas_per_sm = cps;
+    sh->grid = static_cast<uint32_t>(std::max<size_t>(grid, 1));
     return POLAR_OK;
 }
 
@@ -344,6 +223,14 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     }
     LaunchShape sh{};
     polar_status st = choose_shape(c, is_i8, n_frames, device, &sh);
+    if (st != POLAR_OK) return st;
+    CompiledKernel *ck = trace ? nullptr : find_compiled(c, is_i8, sh);
+    int occ = ck ? compiled_occupancy(c, ck, device, sh) : 0;
+    if (occ <= 0) {  // no specialised decoder, or it cannot be resident: interpreter
+        ck = nullptr;
+        occ = occupancy(device, is_i8, sh.stage_channel != 0, sh.threads, sh.smem_bytes);
+    }
+    st = finish_grid(c, is_i8, n_frames, device, occ, &sh);
     if (st != POLAR_OK) return st;
     DeviceState *ds = nullptr;
     st = ensure_device(c, device, &ds);
@@ -384,7 +271,12 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
         }
     }
     a.gscratch = scratch;
-    cudaError_t e = launch_decode(is_i8, trace != nullptr, sh.stage_channel != 0, sh, a, s);
+    cudaError_t e;
+    if (ck) {
+        e = launch_compiled(ck, sh, a, s);
+    } else {
+        e = launch_decode(is_i8, trace != nullptr, sh.stage_channel != 0, sh, a, s);
+    }
     if (scratch) cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -573,15 +465,25 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
                                    uint32_t *threads, uint32_t *smem_stage_max,
                                    uint32_t *warp_stage_max, uint32_t *ctas_per_sm,
                                    uint32_t *stage_channel, uint32_t *grid, size_t *smem_bytes,
-                                   size_t *scratch_bytes) {
+                                   size_t *scratch_bytes, uint32_t *unrolled) {
     if (!code) return POLAR_EINVAL;
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();
         return POLAR_ECUDA;
     }
+    polar_code *c = const_cast<polar_code *>(code);
+    const size_t n = std::max<size_t>(n_frames, 1);
     LaunchShape sh{};
-    polar_status st = choose_shape(code, is_i8 != 0, std::max<size_t>(n_frames, 1), device, &sh);
+    polar_status st = choose_shape(c, is_i8 != 0, n, device, &sh);
+    if (st != POLAR_OK) return st;
+    CompiledKernel *ck = find_compiled(c, is_i8 != 0, sh);
+    int occ = ck ? compiled_occupancy(c, ck, device, sh) : 0;
+    if (occ <= 0) {
+        ck = nullptr;
+        occ = occupancy(device, is_i8 != 0, sh.stage_channel != 0, sh.threads, sh.smem_bytes);
+    }
+    st = finish_grid(c, is_i8 != 0, n, device, occ, &sh);
     if (st != POLAR_OK) return st;
     if (threads) *threads = sh.threads;
     if (smem_stage_max) *smem_stage_max = sh.smem_stage_max;
@@ -591,7 +493,67 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
     if (grid) *grid = sh.grid;
     if (smem_bytes) *smem_bytes = sh.smem_bytes;
     if (scratch_bytes) *scratch_bytes = size_t(sh.grid) * sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
+    if (unrolled) *unrolled = ck ? ck->reg_subtree : 0u;
     return POLAR_OK;
+}
+
+polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
+                                uint32_t reg_subtree) {
+    if (!code) return POLAR_EINVAL;
+    if (reg_subtree == 0) reg_subtree = 256;
+    if (!is_pow2(reg_subtree) || reg_subtree < 32 || reg_subtree > 512) return POLAR_EINVAL;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    if (n_frames == 0) {  // drop every specialised decoder of this LLR type
+        std::lock_guard<std::mutex> g(code->mu);
+        for (auto it = code->compiled.begin(); it != code->compiled.end();) {
+            if (std::get<0>(it->first) == (is_i8 != 0)) {
+                if (it->second.lib) cudaLibraryUnload(it->second.lib);
+                it = code->compiled.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        return POLAR_OK;
+    }
+    LaunchShape sh{};
+    polar_status st = choose_shape(code, is_i8 != 0, n_frames, device, &sh);
+    if (st != POLAR_OK) return st;
+    const CompiledKey key{is_i8 != 0, sh.threads, sh.smem_stage_max, sh.warp_stage_max,
+                          sh.stage_channel};
+    if (find_compiled(code, is_i8 != 0, sh)) return POLAR_OK;
+    // register subtrees always run inside warp-0 runs
+    LaunchShape gsh = sh;
+    gsh.warp_stage_max = std::max(sh.warp_stage_max, reg_subtree);
+    // resident CTAs the shared-memory footprint allows: the register budget of
+    // the generated kernel is capped so that many fit
+    const DeviceProps dp = device_props(device);
+    const size_t per_cta = sh.smem_bytes + 1024;
+    gsh.ctas_per_sm = static_cast<uint32_t>(std::max<size_t>(
+        1, std::min<size_t>({size_t(228 * 1024) / per_cta, size_t(2048 / sh.threads),
+                             size_t(n_frames + dp.sms - 1) / std::max(dp.sms, 1)})));
+    if (code->user[is_i8 ? 1 : 0].ctas_per_sm)
+        gsh.ctas_per_sm = std::min(gsh.ctas_per_sm, code->user[is_i8 ? 1 : 0].ctas_per_sm);
+    CompiledKernel ck;
+    ck.reg_subtree = reg_subtree;
+    std::string log;
+    const std::string src = generate_source(*code, is_i8 != 0, gsh, reg_subtree);
+    const cudaError_t e = compile_source(src, &ck, &log);
+    std::lock_guard<std::mutex> g(code->mu);
+    code->compile_log = log;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    code->compiled[key] = ck;
+    return POLAR_OK;
+}
+
+const char *polar_code_compile_log(const polar_code_t *code) {
+    return code ? code->compile_log.c_str() : "";
 }
 
 polar_status polar_code_check(polar_code_t *code, polar_stream_t stream) {

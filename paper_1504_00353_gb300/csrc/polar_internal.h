@@ -1,48 +1,24 @@
-// Internal types shared by the host side (polar_host.cpp) and the CUDA kernels
-// (polar_kernels.cu) of libpolar_gb300. Not part of the public ABI.
+// Internal types shared by the host side (polar_host.cpp, polar_codegen.cpp) and
+// the CUDA kernels (polar_kernels.cu) of libpolar_gb300. Not part of the public ABI.
+// Device-visible types (op words, KernelArgs, SmemLayout) live in polar_ops.cuh.
 #pragma once
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
 
 #include <cuda_runtime.h>
 
+#include "polar_ops.cuh"
+
 namespace polar {
 
-// Operation kinds of the depth-first Fast-SSC list (Sec. II-D, Listing 1).
-enum OpKind : uint32_t {
-    OP_F = 0,     // alpha_l = f(alpha_v[i], alpha_v[i + N_v/2])          (Eq. 1)
-    OP_G = 1,     // alpha_r = g(alpha_v[i], alpha_v[i + N_v/2], beta_l)  (Eq. 2)
-    OP_G0R = 2,   // G with an all-zero beta_l (left child Rate-0)
-    OP_C = 3,     // beta_v[i] ^= beta_v[i + N_v/2], i < N_v/2            (Eq. 3)
-    OP_C0R = 4,   // beta_v[i] = beta_v[i + N_v/2] (left child Rate-0)
-    OP_R0 = 5,    // beta_v = 0 (Rate-0 right child, or a Rate-0 root)
-    OP_R1 = 6,    // beta_v[i] = alpha_v[i] < 0                           (Eq. 4)
-    OP_REP = 7,   // Repetition: threshold of the folded sum, replicated
-    OP_SPC = 8,   // SPC: hard decisions, flip least-|alpha| bit on odd parity
-};
-
-// One operation as the kernel reads it: a 32-bit word
-//   bits 0-3   kind (OpKind)
-//   bits 4-8   log2(N_v)
-//   bit  9     inside a register-resident subtree (N_v <= kRegSubtree)
-//   bit  10    first op of such a subtree: (N_v, off) is the subtree root
-//   bit  11    last op of such a subtree: store its bits to beta
-//   bits 12-31 off >> log2(N_v), off = index of the node's first leaf
-// Whether an op runs on one warp or on the whole CTA is decided at run time
-// from N_v and the launch's warp_stage_max.
-enum : uint32_t {
-    OPW_REG = 1u << 9,
-    OPW_REG_ENTER = 1u << 10,
-    OPW_REG_EXIT = 1u << 11,
-};
-
-__host__ __device__ inline uint32_t op_kind(uint32_t w) { return w & 0xFu; }
-__host__ __device__ inline uint32_t op_log2n(uint32_t w) { return (w >> 4) & 0x1Fu; }
-__host__ __device__ inline uint32_t op_off(uint32_t w) { return (w >> 12) << op_log2n(w); }
-
-// Largest subtree a warp decodes with its LLRs and bits held in registers.
-constexpr uint32_t kRegSubtree = 32;
+constexpr uint32_t kMaxN = 1u << 20;
+constexpr size_t kMaxDevices = 64;
 
 struct HostOp {
     uint32_t kind, log2n, off, flags;
@@ -60,41 +36,206 @@ struct LaunchShape {
     size_t scratch_elems_per_cta;  // device alpha scratch per CTA (elements)
 };
 
-struct KernelArgs {
-    const uint32_t *ops;           // n_ops packed operation words
-    const uint32_t *trace_offs;    // per op: offset of its F/G/G_0R outputs in a trace row
-    const uint32_t *ext_mask;
-    const uint32_t *ext_pre;
-    const uint32_t *ext_wstart;
-    int *status;
-    const void *llr;
-    uint8_t *out;
-    float *trace;
-    void *gscratch;
-    size_t n_frames;
-    size_t trace_stride;       // floats per frame
-    size_t gstride;            // scratch elements per CTA
-    uint32_t n_ops;
-    uint32_t N, log2N, K;
-    uint32_t S;                // smem_stage_max (already clipped to N/2)
-    uint32_t log2W;            // ops with log2(N_v) <= log2W run on warp 0 alone
-    uint32_t NW;               // beta words (max(1, N/32))
-    uint32_t KW;               // output 32-bit words (ceil(K/32))
-    uint32_t out_row;          // bytes per output row (ceil(K/8))
+struct DeviceState {
+    bool ready = false;
+    int *status = nullptr;
+    uint32_t *tables = nullptr;  // ops | trace_offs | ext_mask | ext_pre | ext_wstart
 };
+
+struct UserLaunch {
+    uint32_t threads = 0, smem_stage_max = 0, warp_stage_max = 0, ctas_per_sm = 0,
+             stage_channel = 0;
+};
+
+// A decoder specialised to one code and launch shape (generated CUDA source
+// compiled with NVRTC): key = (is_i8, threads, S, W, stage_channel).
+using CompiledKey = std::tuple<bool, uint32_t, uint32_t, uint32_t, uint32_t>;
+struct CompiledKernel {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kernel = nullptr;
+    uint32_t reg_subtree = 0;
+    std::map<int, int> occupancy;  // device -> resident CTAs per SM
+    std::map<int, void *> func;    // device -> CUfunction of `kernel` in its primary context
+};
+
+inline int log2u(uint32_t v) {
+    int l = 0;
+    while ((1u << l) < v) ++l;
+    return l;
+}
+
+inline bool is_pow2(uint32_t v) { return v && !(v & (v - 1)); }
 
 // Shared-memory bytes the kernel needs for a shape (alpha, beta, reduction
 // slots, channel buffers and barriers), aligned pieces included.
 size_t kernel_smem_bytes(uint32_t N, uint32_t S, uint32_t threads, bool is_i8,
                          bool stage_channel);
 
-// Maximum resident CTAs per SM for the kernel variant and shape (occupancy API).
+// Maximum resident CTAs per SM for the interpreter variant and shape.
 int kernel_max_ctas_per_sm(bool is_i8, bool stage_channel, uint32_t threads,
                            size_t smem_bytes);
 
-// Launch the decode kernel. Returns the CUDA error of the launch.
+// Raise a kernel's dynamic shared-memory limit to the device maximum (once).
+cudaError_t ensure_smem_limit(const void *k);
+
+// Launch the interpreter kernel. Returns the CUDA error of the launch.
 cudaError_t launch_decode(bool is_i8, bool trace, bool stage_channel,
                           const LaunchShape &shape, const KernelArgs &args,
                           cudaStream_t stream);
 
+}  // namespace polar
+
+// The code handle behind polar_code_t.
+struct polar_code {
+    enum NodeType { NT_R0, NT_R1, NT_REP, NT_SPC, NT_SPLIT };
+
+    uint32_t N = 0, K = 0, log2N = 0, max_rep = UINT32_MAX, max_spc = UINT32_MAX;
+    std::vector<uint8_t> frozen;
+    std::vector<uint32_t> frozen_prefix;  // frozen count in [0, i)
+    std::vector<uint32_t> info_idx;       // A in increasing order
+    std::vector<polar::HostOp> ops;       // interpreter list (register subtrees <= 32)
+    std::vector<uint32_t> trace_off;      // per op (F/G/G_0R), floats
+    size_t trace_len = 0;
+    uint32_t NW = 1, KW = 0;
+    std::vector<uint32_t> ext_mask, ext_pre, ext_wstart;
+    polar::UserLaunch user[2];
+    std::mutex mu;
+    // One slot per device ordinal, sized once so pointers into it stay valid.
+    std::vector<polar::DeviceState> dev = std::vector<polar::DeviceState>(polar::kMaxDevices);
+    std::map<polar::CompiledKey, polar::CompiledKernel> compiled;
+    std::string compile_log;
+
+    // Node type from its leaves, in this order: all frozen -> Rate-0, none
+    // frozen -> Rate-1, only the last leaf information -> Repetition, only the
+    // first leaf frozen -> SPC (Sec. II-D), otherwise split. A size-2 node
+    // [frozen, info] is therefore a Repetition node.
+    NodeType classify(uint32_t off, uint32_t n) const {
+        const uint32_t nf = frozen_prefix[off + n] - frozen_prefix[off];
+        if (nf == n) return NT_R0;
+        if (nf == 0) return NT_R1;
+        if (nf == n - 1 && !frozen[off + n - 1] && n <= max_rep) return NT_REP;
+        if (nf == 1 && frozen[off] && n <= max_spc) return NT_SPC;
+        return NT_SPLIT;
+    }
+
+    // Depth-first operation list of Listing 1. A node with a Rate-0 left child
+    // is G_0R, right subtree, Combine_0R; otherwise F, left subtree, then either
+    // a Rate-0 fill of the right half (no G; Combine leaves beta_l as is) or G,
+    // right subtree, Combine. Every maximal subtree of at most reg_max leaves is
+    // marked as one register-resident subtree (first/last op flagged).
+    std::vector<polar::HostOp> build_ops(uint32_t reg_max) const {
+        std::vector<polar::HostOp> out;
+        build_top(0, N, reg_max, out);
+        return out;
+    }
+
+    void build_top(uint32_t off, uint32_t n, uint32_t reg_max,
+                   std::vector<polar::HostOp> &out) const {
+        if (n > reg_max) {
+            build(off, n, reg_max, true, out);
+            return;
+        }
+        const size_t first = out.size();
+        build(off, n, reg_max, false, out);
+        for (size_t i = first; i < out.size(); ++i) out[i].flags |= polar::OPW_REG;
+        out[first].flags |= polar::OPW_REG_ENTER;
+        out.back().flags |= polar::OPW_REG_EXIT;
+    }
+
+    void build(uint32_t off, uint32_t n, uint32_t reg_max, bool top,
+               std::vector<polar::HostOp> &out) const {
+        auto emit = [&](uint32_t kind, uint32_t size, uint32_t o) {
+            out.push_back(polar::HostOp{kind, static_cast<uint32_t>(polar::log2u(size)), o, 0u});
+        };
+        switch (classify(off, n)) {
+        case NT_R0: emit(polar::OP_R0, n, off); return;
+        case NT_R1: emit(polar::OP_R1, n, off); return;
+        case NT_REP: emit(polar::OP_REP, n, off); return;
+        case NT_SPC: emit(polar::OP_SPC, n, off); return;
+        default: break;
+        }
+        const uint32_t h = n / 2;
+        auto child = [&](uint32_t o) {
+            if (top) build_top(o, h, reg_max, out);
+            else build(o, h, reg_max, false, out);
+        };
+        if (classify(off, h) == NT_R0) {
+            emit(polar::OP_G0R, n, off);
+            child(off + h);
+            emit(polar::OP_C0R, n, off);
+            return;
+        }
+        emit(polar::OP_F, n, off);
+        child(off);
+        if (classify(off + h, h) == NT_R0) {
+            emit(polar::OP_R0, h, off + h);
+            return;
+        }
+        emit(polar::OP_G, n, off);
+        child(off + h);
+        emit(polar::OP_C, n, off);
+    }
+
+    void build_tables() {
+        frozen_prefix.assign(N + 1, 0);
+        for (uint32_t i = 0; i < N; ++i) frozen_prefix[i + 1] = frozen_prefix[i] + frozen[i];
+        info_idx.clear();
+        for (uint32_t i = 0; i < N; ++i)
+            if (!frozen[i]) info_idx.push_back(i);
+        ops = build_ops(polar::kRegSubtree);
+        trace_off.assign(ops.size(), 0);
+        size_t t = 0;
+        for (size_t i = 0; i < ops.size(); ++i) {
+            trace_off[i] = static_cast<uint32_t>(t);
+            if (ops[i].kind <= polar::OP_G0R) t += size_t(1) << (ops[i].log2n - 1);
+        }
+        trace_len = t;
+        // Output packing: beta word w holds leaves [32w, 32w+32).
+        NW = N >= 32 ? N / 32 : 1;
+        KW = (K + 31) / 32;
+        ext_mask.assign(NW, 0);
+        ext_pre.assign(NW, 0);
+        for (uint32_t i = 0; i < N; ++i)
+            if (!frozen[i]) ext_mask[i >> 5] |= 1u << (i & 31);
+        uint32_t pre = 0;
+        for (uint32_t w = 0; w < NW; ++w) {
+            ext_pre[w] = pre;
+            pre += static_cast<uint32_t>(__builtin_popcount(ext_mask[w]));
+        }
+        ext_wstart.assign(KW, 0);
+        uint32_t w = 0;
+        for (uint32_t u = 0; u < KW; ++u) {
+            const uint32_t lo = 32 * u;
+            while (w < NW && ext_pre[w] + static_cast<uint32_t>(__builtin_popcount(ext_mask[w])) <= lo)
+                ++w;
+            ext_wstart[u] = w;
+        }
+    }
+
+    // Packed operation words of the interpreter list (see polar_ops.cuh).
+    std::vector<uint32_t> device_ops() const {
+        std::vector<uint32_t> d(ops.size());
+        for (size_t r = 0; r < ops.size(); ++r) {
+            const polar::HostOp &o = ops[r];
+            d[r] = o.kind | (o.log2n << 4) | o.flags | ((o.off >> o.log2n) << 12);
+        }
+        return d;
+    }
+
+    ~polar_code();
+};
+
+namespace polar {
+// Source text of the decoder specialised to `code` for one launch shape.
+std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
+                            uint32_t reg_subtree);
+// Compile generated source with NVRTC for the current device's architecture and
+// load it. Returns cudaSuccess and fills *out, or an error (log in *log).
+cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::string *log);
+// Resident CTAs per SM of a compiled decoder on the current device (0 on error);
+// also raises its dynamic shared-memory limit to the device maximum.
+int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes);
+// Launch a compiled decoder on the current device.
+cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const KernelArgs &args,
+                            cudaStream_t stream);
 }  // namespace polar

@@ -1,0 +1,915 @@
+// Device building blocks of the Fast-SSC decoder (sm_103a), shared by the
+// operation-list interpreter (polar_kernels.cu, compiled by nvcc) and by the
+// per-code specialised decoders that polar_codegen.cpp emits and compiles at
+// run time with NVRTC. The file therefore includes no host header when
+// __CUDACC_RTC__ is defined.
+//
+// Method: Giard et al., "Low-Latency Software Polar Decoders" (arXiv 1504.00353),
+// Sec. II-C/II-D: min-sum F (Eq. 1), G (Eq. 2) and G_0R, Combine (Eq. 3) and
+// Combine_0R, Rate-0, Rate-1 (Eq. 4), Repetition and SPC nodes.
+//
+// Memory layout (Sec. III-B): the alpha stage of node size n occupies elements
+// [n, 2n) of a per-CTA array, in shared memory for n <= S and in per-CTA
+// device scratch above that; beta is one N-bit array (node (off, n) owns bits
+// [off, off+n), Combine rewrites only the left half), bit-packed in shared
+// memory. float32: F is an exact min with the XOR of the sign bits (beta in
+// {+0,-0}), G adds alpha_v[i] with its sign flipped by beta_l (Listing 3): one
+// IEEE add. int8: G is a saturating add followed by max(-127) (Listing 4).
+// Every operation agrees bit for bit with a scalar evaluation in the same order.
+#pragma once
+
+#ifdef __CUDACC_RTC__
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef unsigned long size_t;
+typedef unsigned long uintptr_t;
+#else
+#include <cstddef>
+#include <cstdint>
+#endif
+
+namespace polar {
+
+// Operation kinds of the depth-first Fast-SSC list (Sec. II-D, Listing 1).
+enum OpKind : uint32_t {
+    OP_F = 0,     // alpha_l = f(alpha_v[i], alpha_v[i + N_v/2])          (Eq. 1)
+    OP_G = 1,     // alpha_r = g(alpha_v[i], alpha_v[i + N_v/2], beta_l)  (Eq. 2)
+    OP_G0R = 2,   // G with an all-zero beta_l (left child Rate-0)
+    OP_C = 3,     // beta_v[i] ^= beta_v[i + N_v/2], i < N_v/2            (Eq. 3)
+    OP_C0R = 4,   // beta_v[i] = beta_v[i + N_v/2] (left child Rate-0)
+    OP_R0 = 5,    // beta_v = 0 (Rate-0 right child, or a Rate-0 root)
+    OP_R1 = 6,    // beta_v[i] = alpha_v[i] < 0                           (Eq. 4)
+    OP_REP = 7,   // Repetition: threshold of the folded sum, replicated
+    OP_SPC = 8,   // SPC: hard decisions, flip least-|alpha| bit on odd parity
+};
+
+// One operation as the interpreter reads it: a 32-bit word
+//   bits 0-3   kind (OpKind)
+//   bits 4-8   log2(N_v)
+//   bit  9     inside a register-resident subtree (N_v <= kRegSubtree)
+//   bit  10    first op of such a subtree: (N_v, off) is the subtree root
+//   bit  11    last op of such a subtree: store its bits to beta
+//   bits 12-31 off >> log2(N_v), off = index of the node's first leaf
+enum : uint32_t {
+    OPW_REG = 1u << 9,
+    OPW_REG_ENTER = 1u << 10,
+    OPW_REG_EXIT = 1u << 11,
+};
+
+__host__ __device__ inline uint32_t op_kind(uint32_t w) { return w & 0xFu; }
+__host__ __device__ inline uint32_t op_log2n(uint32_t w) { return (w >> 4) & 0x1Fu; }
+__host__ __device__ inline uint32_t op_off(uint32_t w) { return (w >> 12) << op_log2n(w); }
+
+// Largest subtree the interpreter decodes in the registers of one warp.
+constexpr uint32_t kRegSubtree = 32;
+
+// Kernel parameters (identical layout for the interpreter and the generated
+// decoders).
+struct KernelArgs {
+    const uint32_t *ops;           // n_ops packed operation words
+    const uint32_t *trace_offs;    // per op: offset of its F/G/G_0R outputs in a trace row
+    const uint32_t *ext_mask;      // info mask of each beta word (NW words)
+    const uint32_t *ext_pre;       // info bits before beta word w (NW words)
+    const uint32_t *ext_wstart;    // first beta word feeding output word u (KW words)
+    int *status;                   // error flags (bit 0: a bounded wait expired)
+    const void *llr;
+    uint8_t *out;
+    float *trace;
+    void *gscratch;
+    size_t n_frames;
+    size_t trace_stride;           // floats per frame
+    size_t gstride;                // scratch elements per CTA
+    uint32_t n_ops;
+    uint32_t N, log2N, K;
+    uint32_t S;                    // smem_stage_max (already clipped to N/2)
+    uint32_t log2W;                // ops with log2(N_v) <= log2W run on warp 0 alone
+    uint32_t NW;                   // beta words (max(1, N/32))
+    uint32_t KW;                   // output 32-bit words (ceil(K/32))
+    uint32_t out_row;              // bytes per output row (ceil(K/8))
+};
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared-memory carve-up, computed identically on host and device.
+struct SmemLayout {
+    size_t alpha, beta, rkey, rpar, chan0, chan1, mbar, total;
+    __host__ __device__ SmemLayout(uint32_t N, uint32_t S, uint32_t es, bool stage) {
+        const uint32_t Se = S < N / 2 ? S : N / 2;
+        const uint32_t NW = N >= 32 ? N / 32 : 1;
+        size_t o = 0;
+        alpha = o;
+        o = align_up(o + size_t(2) * Se * es, 128);
+        beta = o;
+        o = align_up(o + size_t(NW) * 4, 16);
+        rkey = o;
+        o += 32 * 8;
+        rpar = o;
+        o = align_up(o + 32 * 4, 128);
+        chan0 = chan1 = o;
+        if (stage) {
+            chan0 = o;
+            o = align_up(o + size_t(N) * es, 128);
+            chan1 = o;
+            o = align_up(o + size_t(N) * es, 128);
+        }
+        mbar = o;
+        o += 16;
+        total = align_up(o, 16);
+    }
+};
+
+#if defined(__CUDACC__)
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
+constexpr uint32_t kWaitPolls = 1u << 28;              // and at most this many polls
+constexpr uint32_t kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- element ops
+
+__device__ __forceinline__ float f_f32(float a, float b) {
+    const float m = fminf(fabsf(a), fabsf(b));
+    return __uint_as_float(__float_as_uint(m) |
+                           ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u));
+}
+// Eq. 2 with beta_l as the sign bit of alpha_v[i] (Listing 3): one IEEE add.
+__device__ __forceinline__ float g_f32(float a, float b, uint32_t bit) {
+    return b + __uint_as_float(__float_as_uint(a) ^ (bit << 31));
+}
+__device__ __forceinline__ int sat127(int v) { return max(-127, min(127, v)); }
+__device__ __forceinline__ int f_i8s(int a, int b) {
+    const int m = min(abs(a), abs(b));
+    return (a ^ b) < 0 ? -m : m;
+}
+__device__ __forceinline__ int g_i8s(int a, int b, uint32_t bit) {
+    return sat127(bit ? b - a : b + a);
+}
+
+// Element op on the accumulator type (float, or int holding an int8 value).
+__device__ __forceinline__ float op_f(float a, float b) { return f_f32(a, b); }
+__device__ __forceinline__ int op_f(int a, int b) { return f_i8s(a, b); }
+__device__ __forceinline__ float op_g(float a, float b, uint32_t bit) { return g_f32(a, b, bit); }
+__device__ __forceinline__ int op_g(int a, int b, uint32_t bit) { return g_i8s(a, b, bit); }
+__device__ __forceinline__ float op_add(float a, float b) { return a + b; }
+__device__ __forceinline__ int op_add(int a, int b) { return sat127(a + b); }
+__device__ __forceinline__ uint32_t mag_bits(float a) { return __float_as_uint(fabsf(a)); }
+__device__ __forceinline__ uint32_t mag_bits(int a) { return static_cast<uint32_t>(abs(a)); }
+
+// Four int8 lanes per 32-bit word.
+__device__ __forceinline__ uint32_t bytes_from_bits4(uint32_t bits4) {
+    return ((bits4 * 0x00204081u) & 0x01010101u) * 0xFFu;  // bit k -> byte k = 0xFF
+}
+__device__ __forceinline__ uint32_t f_i8x4(uint32_t a, uint32_t b) {
+    const uint32_t m = __vminu4(__vabsss4(a), __vabsss4(b));
+    const uint32_t sel = (((a ^ b) & 0x80808080u) >> 7) * 0xFFu;
+    return (m & ~sel) | (__vneg4(m) & sel);
+}
+__device__ __forceinline__ uint32_t g_i8x4(uint32_t a, uint32_t b, uint32_t bits4) {
+    const uint32_t sel = bytes_from_bits4(bits4);
+    const uint32_t an = (a & ~sel) | (__vneg4(a) & sel);
+    return __vmaxs4(__vaddss4(b, an), 0x81818181u);
+}
+__device__ __forceinline__ uint32_t g0r_i8x4(uint32_t a, uint32_t b) {
+    return __vmaxs4(__vaddss4(b, a), 0x81818181u);
+}
+
+__device__ __forceinline__ bool is_neg(float a) { return a < 0.0f; }
+__device__ __forceinline__ bool is_neg(int8_t a) { return a < 0; }
+
+__device__ __forceinline__ unsigned long long spc_key(float a, uint32_t idx) {
+    return (static_cast<unsigned long long>(__float_as_uint(fabsf(a))) << 32) | idx;
+}
+__device__ __forceinline__ unsigned long long spc_key(int8_t a, uint32_t idx) {
+    return (static_cast<unsigned long long>(abs(static_cast<int>(a))) << 32) | idx;
+}
+
+template <typename T> struct Llr;
+template <> struct Llr<float> {
+    static constexpr uint32_t V = 4;  // elements per 16-byte vector
+    using Acc = float;
+    using Vec = float4;
+};
+template <> struct Llr<int8_t> {
+    static constexpr uint32_t V = 16;
+    using Acc = int;
+    using Vec = uint4;
+};
+
+// ---------------------------------------------------------------- groups
+
+struct WarpGrp {
+    static constexpr bool kCta = false;
+    __device__ static uint32_t rank() { return threadIdx.x & 31u; }
+    __device__ static uint32_t size() { return 32u; }
+    __device__ static void sync() { __syncwarp(); }
+};
+struct CtaGrp {
+    static constexpr bool kCta = true;
+    __device__ static uint32_t rank() { return threadIdx.x; }
+    __device__ static uint32_t size() { return blockDim.x; }
+    __device__ static void sync() { __syncthreads(); }
+};
+
+// ---------------------------------------------------------------- beta helpers
+
+__device__ __forceinline__ uint32_t low_mask(uint32_t n) { return n >= 32 ? kFull : ((1u << n) - 1u); }
+
+// Replace bits [off, off+n) (n <= 32, inside one word) with the low n bits of v.
+__device__ __forceinline__ void write_field(uint32_t *beta, uint32_t off, uint32_t n, uint32_t v) {
+    if (n >= 32) {
+        beta[off >> 5] = v;
+        return;
+    }
+    const uint32_t p = off & 31u;
+    const uint32_t fm = ((1u << n) - 1u) << p;
+    uint32_t w = beta[off >> 5];
+    w = (w & ~fm) | ((v << p) & fm);
+    beta[off >> 5] = w;
+}
+
+__device__ __forceinline__ uint32_t bits_at(const uint32_t *beta, uint32_t pos, uint32_t nbits) {
+    const uint32_t w = beta[pos >> 5] >> (pos & 31u);
+    return nbits >= 32 ? w : (w & ((1u << nbits) - 1u));
+}
+
+// ---------------------------------------------------------------- F / G / G_0R in memory
+
+template <uint32_t KIND>
+__device__ __forceinline__ float4 fg4(float4 a, float4 b, uint32_t bits) {
+    float4 r;
+    if (KIND == OP_F) {
+        r.x = f_f32(a.x, b.x); r.y = f_f32(a.y, b.y); r.z = f_f32(a.z, b.z); r.w = f_f32(a.w, b.w);
+    } else if (KIND == OP_G) {
+        r.x = g_f32(a.x, b.x, bits & 1u);
+        r.y = g_f32(a.y, b.y, (bits >> 1) & 1u);
+        r.z = g_f32(a.z, b.z, (bits >> 2) & 1u);
+        r.w = g_f32(a.w, b.w, (bits >> 3) & 1u);
+    } else {
+        r.x = b.x + a.x; r.y = b.y + a.y; r.z = b.z + a.z; r.w = b.w + a.w;
+    }
+    return r;
+}
+template <uint32_t KIND>
+__device__ __forceinline__ uint4 fg4(uint4 a, uint4 b, uint32_t bits) {
+    uint4 r;
+    if (KIND == OP_F) {
+        r.x = f_i8x4(a.x, b.x); r.y = f_i8x4(a.y, b.y); r.z = f_i8x4(a.z, b.z); r.w = f_i8x4(a.w, b.w);
+    } else if (KIND == OP_G) {
+        r.x = g_i8x4(a.x, b.x, bits & 0xFu);
+        r.y = g_i8x4(a.y, b.y, (bits >> 4) & 0xFu);
+        r.z = g_i8x4(a.z, b.z, (bits >> 8) & 0xFu);
+        r.w = g_i8x4(a.w, b.w, (bits >> 12) & 0xFu);
+    } else {
+        r.x = g0r_i8x4(a.x, b.x); r.y = g0r_i8x4(a.y, b.y); r.z = g0r_i8x4(a.z, b.z); r.w = g0r_i8x4(a.w, b.w);
+    }
+    return r;
+}
+
+template <uint32_t KIND, typename T>
+__device__ __forceinline__ T fg_scalar(T a, T b, uint32_t bit) {
+    using Acc = typename Llr<T>::Acc;
+    const Acc x = a, y = b;
+    return static_cast<T>(KIND == OP_F ? op_f(x, y) : (KIND == OP_G ? op_g(x, y, bit) : op_add(x, y)));
+}
+
+// out[i] = op(in[i], in[i + h]) for i < h; in and out never overlap. Four vectors
+// per thread are loaded before any is used, so device-memory operands (the
+// channel at the root, scratch stages) overlap their latency.
+template <typename T, class Grp, uint32_t KIND>
+__device__ __forceinline__ void op_fg(const T *__restrict__ in, T *__restrict__ out, uint32_t h,
+                                      const uint32_t *beta, uint32_t o) {
+    using Vec = typename Llr<T>::Vec;
+    constexpr uint32_t V = Llr<T>::V;
+    if (h >= V) {
+        const uint32_t nv = h / V, G = Grp::size();
+        const Vec *va = reinterpret_cast<const Vec *>(in);
+        const Vec *vb = reinterpret_cast<const Vec *>(in + h);
+        Vec *vo = reinterpret_cast<Vec *>(out);
+        uint32_t v = Grp::rank();
+        for (; v + 3 * G < nv; v += 4 * G) {
+            Vec a[4], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                a[k] = va[v + k * G];
+                b[k] = vb[v + k * G];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t bits = KIND == OP_G ? bits_at(beta, o + (v + k * G) * V, V) : 0u;
+                vo[v + k * G] = fg4<KIND>(a[k], b[k], bits);
+            }
+        }
+        for (; v < nv; v += G) {
+            const uint32_t bits = KIND == OP_G ? bits_at(beta, o + v * V, V) : 0u;
+            vo[v] = fg4<KIND>(va[v], vb[v], bits);
+        }
+    } else {
+        for (uint32_t i = Grp::rank(); i < h; i += Grp::size()) {
+            const uint32_t bit = KIND == OP_G ? bits_at(beta, o + i, 1) : 0u;
+            out[i] = fg_scalar<KIND, T>(in[i], in[i + h], bit);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Combine / Rate-0 in memory
+
+template <class Grp>
+__device__ __forceinline__ void op_combine(uint32_t *beta, uint32_t n, uint32_t o, bool copy) {
+    const uint32_t h = n >> 1;
+    if (h >= 32) {
+        const uint32_t wl = o >> 5, wr = (o + h) >> 5, nw = h >> 5;
+        for (uint32_t j = Grp::rank(); j < nw; j += Grp::size()) {
+            const uint32_t r = beta[wr + j];
+            beta[wl + j] = copy ? r : (beta[wl + j] ^ r);
+        }
+    } else if (Grp::rank() == 0) {
+        const uint32_t p = o & 31u, fm = (1u << h) - 1u;
+        uint32_t w = beta[o >> 5];
+        const uint32_t r = (w >> (p + h)) & fm;
+        const uint32_t l = copy ? r : (((w >> p) & fm) ^ r);
+        beta[o >> 5] = (w & ~(fm << p)) | (l << p);
+    }
+}
+
+template <class Grp>
+__device__ __forceinline__ void op_r0(uint32_t *beta, uint32_t n, uint32_t o) {
+    if (n >= 32) {
+        for (uint32_t j = Grp::rank(); j < (n >> 5); j += Grp::size()) beta[(o >> 5) + j] = 0u;
+    } else if (Grp::rank() == 0) {
+        write_field(beta, o, n, 0u);
+    }
+}
+
+// ---------------------------------------------------------------- node decoders in memory
+
+// Rate-1 (Eq. 4): one ballot per 32 consecutive elements; four chunks loaded ahead.
+template <typename T, class Grp>
+__device__ __forceinline__ void op_r1(const T *__restrict__ in, uint32_t *beta, uint32_t n,
+                                      uint32_t o) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t w0 = Grp::kCta ? (threadIdx.x >> 5) : 0u;
+    const uint32_t ws = Grp::kCta ? (blockDim.x >> 5) : 1u;
+    const uint32_t nch = (n + 31u) >> 5;
+    uint32_t c = w0;
+    for (; c + 3 * ws < nch; c += 4 * ws) {
+        T a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = in[((c + k * ws) << 5) + lane];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t bal = __ballot_sync(kFull, is_neg(a[k]));
+            if (lane == 0) beta[(o >> 5) + c + k * ws] = bal;
+        }
+    }
+    for (; c < nch; c += ws) {
+        const uint32_t idx = (c << 5) + lane;
+        const bool neg = idx < n && is_neg(in[idx]);
+        const uint32_t bal = __ballot_sync(kFull, neg);
+        if (lane == 0) write_field(beta, o + (c << 5), n < 32 ? n : 32, bal);
+    }
+}
+
+// SPC: hard decisions, their parity, flip the least-|alpha| (lowest index)
+// decision when the parity is odd (Listing 2 returns the first lane equal to
+// the minimum).
+template <typename T, class Grp>
+__device__ __forceinline__ void op_spc(const T *__restrict__ in, uint32_t *beta, uint32_t n,
+                                       uint32_t o, unsigned long long *rkey, uint32_t *rpar) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t w0 = Grp::kCta ? (threadIdx.x >> 5) : 0u;
+    const uint32_t ws = Grp::kCta ? (blockDim.x >> 5) : 1u;
+    const uint32_t nch = (n + 31u) >> 5;
+    unsigned long long kmin = ~0ull;
+    uint32_t par = 0;
+    uint32_t c = w0;
+    for (; c + 3 * ws < nch; c += 4 * ws) {
+        T a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = in[((c + k * ws) << 5) + lane];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t bal = __ballot_sync(kFull, is_neg(a[k]));
+            par ^= __popc(bal) & 1u;
+            if (lane == 0) beta[(o >> 5) + c + k * ws] = bal;
+            const unsigned long long key = spc_key(a[k], ((c + k * ws) << 5) + lane);
+            kmin = key < kmin ? key : kmin;
+        }
+    }
+    for (; c < nch; c += ws) {
+        const uint32_t idx = (c << 5) + lane;
+        const bool valid = idx < n;
+        const T a = valid ? in[idx] : T(0);
+        const uint32_t bal = __ballot_sync(kFull, valid && is_neg(a));
+        par ^= __popc(bal) & 1u;
+        if (lane == 0) write_field(beta, o + (c << 5), n < 32 ? n : 32, bal);
+        if (valid) {
+            const unsigned long long key = spc_key(a, idx);
+            kmin = key < kmin ? key : kmin;
+        }
+    }
+#pragma unroll
+    for (uint32_t s = 16; s > 0; s >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(kFull, kmin, s);
+        kmin = t < kmin ? t : kmin;
+    }
+    if (Grp::kCta) {
+        const uint32_t w = threadIdx.x >> 5;
+        if (lane == 0) {
+            rkey[w] = kmin;
+            rpar[w] = par;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t p = 0;
+            for (uint32_t i = 0; i < ws; ++i) {
+                kmin = rkey[i] < kmin ? rkey[i] : kmin;
+                p ^= rpar[i];
+            }
+            if (p) {
+                const uint32_t pos = o + static_cast<uint32_t>(kmin & 0xffffffffull);
+                beta[pos >> 5] ^= 1u << (pos & 31u);
+            }
+        }
+    } else if (lane == 0 && par) {
+        const uint32_t pos = o + static_cast<uint32_t>(kmin & 0xffffffffull);
+        beta[pos >> 5] ^= 1u << (pos & 31u);
+    }
+}
+
+// Repetition: the sum of alpha_v folded as t[i] <- t[i] + t[i + m],
+// m = n/2, n/4, ..., 1 (the G_0R chain SC computes on this node); the bit is
+// (sum < 0), replicated. Folds above 64 values run in memory (tmp = the free
+// stage n/2), the last ones as warp shuffles with the same pairing.
+template <typename T, class Grp>
+__device__ __forceinline__ void op_rep(const T *in, T *tmp, uint32_t *beta, uint32_t n,
+                                       uint32_t o) {
+    using Acc = typename Llr<T>::Acc;
+    uint32_t len = n;
+    const T *src = in;
+    while (len > 64) {
+        const uint32_t m = len >> 1;
+        if (src == tmp) {
+            for (uint32_t i = Grp::rank(); i < m; i += Grp::size())
+                tmp[i] = fg_scalar<OP_G0R, T>(tmp[i], tmp[i + m], 0u);
+        } else {
+            op_fg<T, Grp, OP_G0R>(src, tmp, m, nullptr, 0);
+        }
+        Grp::sync();
+        src = tmp;
+        len = m;
+    }
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        Acc x;
+        uint32_t cur;
+        if (len == 64) {
+            x = op_add(static_cast<Acc>(src[lane]), static_cast<Acc>(src[lane + 32]));
+            cur = 32;
+        } else {
+            x = lane < len ? static_cast<Acc>(src[lane]) : Acc(0);
+            cur = len;
+        }
+        while (cur > 1) {
+            cur >>= 1;
+            const Acc y = __shfl_down_sync(kFull, x, cur);
+            if (lane < cur) x = op_add(x, y);
+        }
+        const Acc s = __shfl_sync(kFull, x, 0);
+        const uint32_t word = s < Acc(0) ? kFull : 0u;
+        if (n >= 32) {
+            for (uint32_t j = lane; j < (n >> 5); j += 32) beta[(o >> 5) + j] = word;
+        } else if (lane == 0) {
+            write_field(beta, o, n, word);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- frame state
+
+template <typename T>
+struct Frame {
+    const T *chan;     // channel LLRs of the frame (shared or device memory)
+    T *s_alpha;        // shared alpha array (stage n at [n, 2n), n <= S)
+    T *g_alpha;        // device scratch (stage n at [n - 2S, 2n - 2S), n > S)
+    uint32_t *beta;    // shared beta bits
+    unsigned long long *rkey;
+    uint32_t *rpar;
+    uint32_t N, S;
+    __device__ __forceinline__ const T *stage_in(uint32_t n) const {
+        return n == N ? chan : (n <= S ? s_alpha + n : g_alpha + (n - 2 * S));
+    }
+    __device__ __forceinline__ T *stage(uint32_t n) const {
+        return n <= S ? s_alpha + n : g_alpha + (n - 2 * S);
+    }
+};
+
+template <typename T, class Grp>
+__device__ __forceinline__ void exec_op(uint32_t kind, uint32_t n, uint32_t o, const Frame<T> &fr) {
+    switch (kind) {
+    case OP_F: op_fg<T, Grp, OP_F>(fr.stage_in(n), fr.stage(n >> 1), n >> 1, fr.beta, o); break;
+    case OP_G: op_fg<T, Grp, OP_G>(fr.stage_in(n), fr.stage(n >> 1), n >> 1, fr.beta, o); break;
+    case OP_G0R: op_fg<T, Grp, OP_G0R>(fr.stage_in(n), fr.stage(n >> 1), n >> 1, fr.beta, o); break;
+    case OP_C: op_combine<Grp>(fr.beta, n, o, false); break;
+    case OP_C0R: op_combine<Grp>(fr.beta, n, o, true); break;
+    case OP_R0: op_r0<Grp>(fr.beta, n, o); break;
+    case OP_R1: op_r1<T, Grp>(fr.stage_in(n), fr.beta, n, o); break;
+    case OP_REP: op_rep<T, Grp>(fr.stage_in(n), fr.stage(n >> 1), fr.beta, n, o); break;
+    default: op_spc<T, Grp>(fr.stage_in(n), fr.beta, n, o, fr.rkey, fr.rpar); break;
+    }
+}
+
+// Software bit extract: the bits of x selected by m, packed to the bottom.
+__device__ __forceinline__ uint32_t pext32(uint32_t x, uint32_t m) {
+    if (m == kFull) return x;
+    uint32_t r = 0, k = 0;
+    while (m) {
+        const uint32_t b = m & (0u - m);
+        r |= ((x & b) ? 1u : 0u) << k;
+        ++k;
+        m ^= b;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- bulk copy
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for the phase with the given parity; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t i = 0; i < kWaitPolls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (ok) return true;
+        if ((i & 63u) == 63u && globaltimer() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- frame loop
+
+// Persistent loop over the frames of a launch: frame f goes to CTA f % grid.
+// For each frame `body(fr, trace_row)` runs the operation list; afterwards the
+// estimate x_hat restricted to A is packed LSB first (output word u = info bits
+// [32u, 32u+32)). With STAGE the frame's LLRs are brought into shared memory
+// by cp.async.bulk, two frames ahead of use.
+template <typename T, bool TRACE, bool STAGE, class Body>
+__device__ __forceinline__ void run_frames(const KernelArgs &a, const Body &body) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout L(a.N, a.S, sizeof(T), STAGE);
+    const uint32_t tid = threadIdx.x;
+
+    Frame<T> fr;
+    fr.s_alpha = reinterpret_cast<T *>(smem + L.alpha);
+    fr.g_alpha = a.gscratch ? static_cast<T *>(a.gscratch) + size_t(blockIdx.x) * a.gstride
+                            : nullptr;
+    fr.beta = reinterpret_cast<uint32_t *>(smem + L.beta);
+    fr.rkey = reinterpret_cast<unsigned long long *>(smem + L.rkey);
+    fr.rpar = reinterpret_cast<uint32_t *>(smem + L.rpar);
+    fr.N = a.N;
+    fr.S = a.S;
+
+    T *const chan0 = reinterpret_cast<T *>(smem + L.chan0);
+    T *const chan1 = reinterpret_cast<T *>(smem + L.chan1);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
+    const uint32_t chan_bytes = a.N * static_cast<uint32_t>(sizeof(T));
+    const T *llr = static_cast<const T *>(a.llr);
+    const size_t G = gridDim.x;
+
+    if (STAGE) {
+        if (tid == 0) {
+            mbar_init(&mbar[0]);
+            mbar_init(&mbar[1]);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if (blockIdx.x < a.n_frames)
+                bulk_load(chan0, llr + size_t(blockIdx.x) * a.N, chan_bytes, &mbar[0]);
+            if (blockIdx.x + G < a.n_frames)
+                bulk_load(chan1, llr + (blockIdx.x + G) * a.N, chan_bytes, &mbar[1]);
+        }
+        __syncthreads();
+    }
+
+    uint32_t it = 0;
+    for (size_t f = blockIdx.x; f < a.n_frames; f += G, ++it) {
+        if (STAGE) {
+            const uint32_t b = it & 1u;
+            const bool bad = !mbar_wait(&mbar[b], (it >> 1) & 1u);
+            if (__syncthreads_or(bad)) {
+                if (tid == 0) atomicOr(a.status, 1);
+                // let any copy still in flight land before the CTA's shared memory is released
+                mbar_wait(&mbar[b], (it >> 1) & 1u);
+                if (f + G < a.n_frames) mbar_wait(&mbar[b ^ 1u], ((it + 1) >> 1) & 1u);
+                return;
+            }
+            fr.chan = b ? chan1 : chan0;
+        } else {
+            fr.chan = llr + f * a.N;
+        }
+        float *trace_row = TRACE ? a.trace + f * a.trace_stride : nullptr;
+
+        body(fr, trace_row);
+
+        uint8_t *out = a.out + f * a.out_row;
+        for (uint32_t u = tid; u < a.KW; u += blockDim.x) {
+            const uint32_t lo = u << 5;
+            const uint32_t hi = min(lo + 32u, a.K);
+            uint32_t acc = 0;
+            for (uint32_t w = __ldg(a.ext_wstart + u); w < a.NW; ++w) {
+                const uint32_t pre = __ldg(a.ext_pre + w);
+                if (pre >= hi) break;
+                const uint32_t m = __ldg(a.ext_mask + w);
+                if (!m) continue;
+                const uint32_t e = pext32(fr.beta[w], m);
+                const int pos = static_cast<int>(pre) - static_cast<int>(lo);
+                acc |= pos >= 0 ? (e << pos) : (e >> (-pos));
+            }
+            if (hi - lo < 32) acc &= (1u << (hi - lo)) - 1u;
+            const uint32_t nb = min(4u, a.out_row - 4u * u);
+            uint8_t *dst = out + 4u * u;
+            if (nb == 4 && (reinterpret_cast<uintptr_t>(dst) & 3u) == 0) {
+                *reinterpret_cast<uint32_t *>(dst) = acc;
+            } else {
+                for (uint32_t b = 0; b < nb; ++b) dst[b] = static_cast<uint8_t>(acc >> (8 * b));
+            }
+        }
+        __syncthreads();
+
+        if (STAGE && tid == 0 && f + 2 * G < a.n_frames) {
+            // every thread is done reading this buffer (barrier above); order those
+            // generic-proxy reads before the async-proxy write of the next frame
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_load((it & 1u) ? chan1 : chan0, llr + (f + 2 * G) * a.N, chan_bytes,
+                      &mbar[it & 1u]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- specialised subtrees
+
+// Compile-time loop: f(UC<I>{}) for I in [B, E). Indices reach the body as
+// template constants, so arrays indexed by them stay in registers.
+template <uint32_t V> struct UC {
+    static constexpr uint32_t value = V;
+};
+template <uint32_t B, uint32_t E, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(UC<B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Subtree of at most R leaves decoded by warp 0 with compile-time node sizes and
+// offsets (the generated decoders): stage m >= 32 is m/32 registers per lane
+// (element j + 32k in register k of lane j), stages 1..16 share register A
+// (stage m element j on lane m + j), and the subtree's bits are R/32 words held
+// identically by every lane (word k = leaves [32k, 32k + 32) of the subtree).
+// F and G above 32 leaves are lane-local; at 32 and below they are shuffles.
+template <typename T, uint32_t R>
+struct RegSub {
+    using Acc = typename Llr<T>::Acc;
+    static constexpr uint32_t NWORD = R >= 32 ? R / 32 : 1;
+    Acc s512[16], s256[8], s128[4], s64[2], s32, A;
+    uint32_t bw[NWORD];
+    uint32_t lane;
+
+    template <uint32_t m, uint32_t k>
+    __device__ __forceinline__ Acc &reg() {
+        if constexpr (m == 512) return s512[k];
+        else if constexpr (m == 256) return s256[k];
+        else if constexpr (m == 128) return s128[k];
+        else if constexpr (m == 64) return s64[k];
+        else return s32;
+    }
+
+    // Load the subtree root's LLRs (stage n0) from memory.
+    template <uint32_t n0>
+    __device__ __forceinline__ void enter(const T *src) {
+        if constexpr (n0 >= 32) {
+            static_for<0, n0 / 32>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                reg<n0, k>() = static_cast<Acc>(src[32 * k + lane]);
+            });
+        } else {
+            A = (lane >= n0 && lane < 2 * n0) ? static_cast<Acc>(src[(lane - n0) & 31u]) : Acc(0);
+        }
+    }
+
+    // Store the subtree's n0 bits at leaf offset o0 of beta.
+    template <uint32_t n0>
+    __device__ __forceinline__ void exit(uint32_t *beta, uint32_t o0) {
+        if constexpr (n0 >= 32) {
+            static_for<0, n0 / 32>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                if (lane == k) beta[(o0 >> 5) + k] = bw[k];
+            });
+        } else {
+            if (lane == 0) write_field(beta, o0, n0, bw[0]);
+        }
+    }
+
+    template <uint32_t w, uint32_t q, uint32_t width>
+    __device__ __forceinline__ void set_field(uint32_t v) {
+        if constexpr (width >= 32) {
+            bw[w] = v;
+        } else {
+            constexpr uint32_t fm = ((1u << width) - 1u) << q;
+            bw[w] = (bw[w] & ~fm) | ((v << q) & fm);
+        }
+    }
+
+    // F / G / G_0R of a node of n leaves at subtree offset p.
+    template <uint32_t KIND, uint32_t n, uint32_t p>
+    __device__ __forceinline__ void fg() {
+        if constexpr (n >= 64) {
+            constexpr uint32_t K = n / 64;
+            static_for<0, K>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                const Acc x = reg<n, k>(), y = reg<n, k + K>();
+                Acc r;
+                if constexpr (KIND == OP_F) r = op_f(x, y);
+                else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32 + k] >> lane) & 1u);
+                else r = op_add(x, y);
+                reg<n / 2, k>() = r;
+            });
+        } else if constexpr (n == 32) {
+            // output element i = lane - 16 (lanes 16..31) from s32 of lanes i and i + 16
+            const Acc x = __shfl_up_sync(kFull, s32, 16);
+            const Acc y = s32;
+            Acc r;
+            if constexpr (KIND == OP_F) r = op_f(x, y);
+            else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32] >> ((lane - 16) & 31u)) & 1u);
+            else r = op_add(x, y);
+            if (lane >= 16) A = r;
+        } else {
+            constexpr uint32_t h = n / 2, q = p % 32;
+            // output element i = lane - h (lanes [h, 2h)) from lanes n + i and n + i + h
+            const Acc x = __shfl_down_sync(kFull, A, h);
+            const Acc y = __shfl_down_sync(kFull, A, n);
+            Acc r;
+            if constexpr (KIND == OP_F) r = op_f(x, y);
+            else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32] >> ((q + lane - h) & 31u)) & 1u);
+            else r = op_add(x, y);
+            if (lane >= h && lane < 2 * h) A = r;
+        }
+    }
+
+    // Combine (copy = false) / Combine_0R (copy = true) of a node of n leaves at p.
+    template <uint32_t n, uint32_t p, bool copy>
+    __device__ __forceinline__ void combine() {
+        constexpr uint32_t h = n / 2;
+        if constexpr (h >= 32) {
+            static_for<0, h / 32>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                const uint32_t r = bw[(p + h) / 32 + k];
+                bw[p / 32 + k] = copy ? r : (bw[p / 32 + k] ^ r);
+            });
+        } else {
+            constexpr uint32_t w = p / 32, q = p % 32, m = (1u << h) - 1u;
+            const uint32_t l = (bw[w] >> q) & m, r = (bw[w] >> (q + h)) & m;
+            set_field<w, q, h>(copy ? r : (l ^ r));
+        }
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void r0() {
+        if constexpr (n >= 32) {
+            static_for<0, n / 32>([&](auto kc) { bw[p / 32 + decltype(kc)::value] = 0u; });
+        } else {
+            set_field<p / 32, p % 32, n>(0u);
+        }
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void r1() {
+        if constexpr (n >= 32) {
+            static_for<0, n / 32>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                bw[p / 32 + k] = __ballot_sync(kFull, reg<n, k>() < Acc(0));
+            });
+        } else {
+            const bool in = lane >= n && lane < 2 * n;
+            set_field<p / 32, p % 32, n>(__ballot_sync(kFull, in && A < Acc(0)) >> n);
+        }
+    }
+
+    // Folds t[k] <- t[k] + t[k + m] for m = K/2, ..., 1 over K lane-local values.
+    template <uint32_t K>
+    __device__ __forceinline__ void fold_local(Acc (&t)[K]) {
+        if constexpr (K > 1) {
+            static_for<0, K / 2>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                t[k] = op_add(t[k], t[k + K / 2]);
+            });
+            fold_local<K / 2>(reinterpret_cast<Acc(&)[K / 2]>(t));
+        }
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void rep() {
+        Acc x;
+        if constexpr (n >= 32) {
+            constexpr uint32_t K = n / 32;
+            Acc t[K];
+            static_for<0, K>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                t[k] = reg<n, k>();
+            });
+            // lane-local folds t[e] += t[e + m] for m = n/2 .. 32 (e = lane + 32k)
+            fold_local<K>(t);
+            x = t[0];
+#pragma unroll
+            for (uint32_t m = 16; m >= 1; m /= 2) {
+                const Acc y = __shfl_down_sync(kFull, x, m);
+                if (lane < m) x = op_add(x, y);
+            }
+            x = __shfl_sync(kFull, x, 0);
+            const uint32_t word = x < Acc(0) ? kFull : 0u;
+            static_for<0, n / 32>([&](auto kc) { bw[p / 32 + decltype(kc)::value] = word; });
+        } else {
+            x = A;
+#pragma unroll
+            for (uint32_t m = n / 2; m >= 1; m /= 2) {
+                const Acc y = __shfl_down_sync(kFull, x, m);
+                if (lane >= n && lane < n + m) x = op_add(x, y);
+            }
+            x = __shfl_sync(kFull, x, n);
+            set_field<p / 32, p % 32, n>(x < Acc(0) ? kFull : 0u);
+        }
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void spc() {
+        if constexpr (n >= 32) {
+            constexpr uint32_t K = n / 32;
+            uint32_t par = 0, mk = kFull;
+            static_for<0, K>([&](auto kc) {
+                constexpr uint32_t k = decltype(kc)::value;
+                const uint32_t hd = __ballot_sync(kFull, reg<n, k>() < Acc(0));
+                bw[p / 32 + k] = hd;
+                par ^= __popc(hd);
+                const uint32_t mg = mag_bits(reg<n, k>());
+                mk = mg < mk ? mg : mk;
+            });
+            const uint32_t mn = __reduce_min_sync(kFull, mk);
+            uint32_t e = kFull;  // lowest element index of this lane with |alpha| == mn
+            static_for<0, K>([&](auto kc) {
+                constexpr uint32_t k = K - 1 - decltype(kc)::value;
+                if (mag_bits(reg<n, k>()) == mn) e = 32 * k + lane;
+            });
+            e = __reduce_min_sync(kFull, e);
+            if (par & 1u) {
+                static_for<0, K>([&](auto kc) {
+                    constexpr uint32_t k = decltype(kc)::value;
+                    if ((e >> 5) == k) bw[p / 32 + k] ^= 1u << (e & 31u);
+                });
+            }
+        } else {
+            const bool in = lane >= n && lane < 2 * n;
+            const uint32_t hd = __ballot_sync(kFull, in && A < Acc(0)) >> n;
+            const uint32_t mag = in ? mag_bits(A) : kFull;
+            const uint32_t mn = __reduce_min_sync(kFull, mag);
+            const uint32_t first = (__ffs(__ballot_sync(kFull, in && mag == mn)) - 1u - n) & 31u;
+            set_field<p / 32, p % 32, n>(hd ^ ((__popc(hd) & 1u) << first));
+        }
+    }
+};
+
+// Pointer to stage n of a generated decoder with compile-time N and S.
+template <typename T, uint32_t N, uint32_t S, uint32_t n>
+__device__ __forceinline__ const T *gen_in(const Frame<T> &fr) {
+    if constexpr (n == N) return fr.chan;
+    else if constexpr (n <= S) return fr.s_alpha + n;
+    else return fr.g_alpha + (n - 2 * S);
+}
+template <typename T, uint32_t S, uint32_t n>
+__device__ __forceinline__ T *gen_out(const Frame<T> &fr) {
+    if constexpr (n <= S) return fr.s_alpha + n;
+    else return fr.g_alpha + (n - 2 * S);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace polar

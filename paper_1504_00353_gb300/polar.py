@@ -24,7 +24,7 @@ EXPORTS = [
     "polar_status_str", "polar_code_create", "polar_code_create_ex", "polar_code_destroy",
     "polar_code_info", "polar_code_schedule", "polar_encode_systematic", "polar_decode",
     "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
-    "polar_code_get_launch", "polar_code_check",
+    "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_log",
 ]
 
 
@@ -57,7 +57,9 @@ def _load():
         "polar_code_trace_len": ([vp], sz),
         "polar_decode_trace": ([vp, vp, st, vp, vp, sz, vp], st),
         "polar_code_set_launch": ([vp, st, u32, u32, u32, u32, u32], st),
-        "polar_code_get_launch": ([vp, st, sz, u32p, u32p, u32p, u32p, u32p, u32p, szp, szp], st),
+        "polar_code_get_launch": ([vp, st, sz, u32p, u32p, u32p, u32p, u32p, u32p, szp, szp, u32p], st),
+        "polar_code_compile": ([vp, st, sz, u32], st),
+        "polar_code_compile_log": ([vp], ctypes.c_char_p),
         "polar_code_check": ([vp, vp], st),
     }
     for name, (args, res) in sig.items():
@@ -228,13 +230,27 @@ def polar_code_set_launch(code: PolarCode, is_i8: bool, threads=0, smem_stage_ma
 def polar_code_get_launch(code: PolarCode, is_i8: bool, n_frames: int) -> dict:
     v = [ctypes.c_uint32() for _ in range(6)]
     s = [ctypes.c_size_t() for _ in range(2)]
+    unrolled = ctypes.c_uint32()
     _check(_lib.polar_code_get_launch(code.handle, int(bool(is_i8)), n_frames,
-                                      *[ctypes.byref(x) for x in v], *[ctypes.byref(x) for x in s]),
+                                      *[ctypes.byref(x) for x in v], *[ctypes.byref(x) for x in s],
+                                      ctypes.byref(unrolled)),
            "polar_code_get_launch")
     keys = ["threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm", "stage_channel", "grid"]
     d = {k: x.value for k, x in zip(keys, v)}
     d["smem_bytes"], d["scratch_bytes"] = s[0].value, s[1].value
+    d["unrolled"] = unrolled.value
     return d
+
+
+def polar_code_compile(code: PolarCode, is_i8: bool, n_frames: int, reg_subtree: int = 0):
+    """Compile the decoder specialised to this code for the shape of an n_frames decode."""
+    st = _lib.polar_code_compile(code.handle, int(bool(is_i8)), n_frames, reg_subtree)
+    if st != 0:
+        raise PolarError(st, "polar_code_compile: " + polar_code_compile_log(code)[-2000:])
+
+
+def polar_code_compile_log(code: PolarCode) -> str:
+    return (_lib.polar_code_compile_log(code.handle) or b"").decode(errors="replace")
 
 
 def polar_code_check(code: PolarCode, stream=None):

@@ -1,0 +1,79 @@
+"""Specialised (code-unrolled) decoders vs the CPU oracle: the decoder generated
+for one code and compiled at run time must give the same bits as the oracle
+(and so as the operation-list interpreter) for float32 and int8 LLRs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1504_00353_gb300 import polar, synth
+from tests import _cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def decode(code, y, i8):
+    t = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    out = (polar.polar_decode_i8 if i8 else polar.polar_decode)(code, t)
+    torch.cuda.synchronize()
+    polar.polar_code_check(code)
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("i8", [False, True])
+@pytest.mark.parametrize("n_frames", [1, 10000])
+def test_n1024_unrolled(i8, n_frames):
+    mask, d, llr = _cases.frames(1024, 512, 2.5, n_frames, seed=30, distinct=500)
+    y = synth.quantize_i8(llr) if i8 else llr
+    code = polar.polar_code_create(1024, 512, mask)
+    assert polar.polar_code_get_launch(code, i8, n_frames)["unrolled"] == 0
+    polar.polar_code_compile(code, i8, n_frames)
+    assert polar.polar_code_get_launch(code, i8, n_frames)["unrolled"] == 256
+    assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y))
+
+
+@pytest.mark.parametrize("N,reg", [(8, 32), (64, 64), (512, 256), (4096, 512), (2048, 32)])
+def test_random_masks_unrolled(N, reg):
+    rng = np.random.default_rng(N + reg)
+    K = int(rng.integers(1, N))
+    mask = _cases.random_mask(rng, N, K)
+    ms = int(rng.choice([0, 16, oracle.UNLIMITED]))
+    code = polar.polar_code_create(N, K, mask, max_spc=ms)
+    llr = (rng.standard_normal((200, N)) * 3).astype(np.float32)
+    yi = rng.integers(-127, 128, (200, N)).astype(np.int8)
+    for y, i8 in ((llr, False), (yi, True)):
+        polar.polar_code_compile(code, i8, 200, reg)
+        assert polar.polar_code_get_launch(code, i8, 200)["unrolled"] == reg
+        assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y, max_spc=ms))
+
+
+@pytest.mark.parametrize("i8", [False, True])
+def test_n32768_unrolled_batch4096_sampled(i8):
+    mask, d, llr = _cases.frames(32768, 29492, 4.0, 4096, seed=31, distinct=64)
+    y = synth.quantize_i8(llr) if i8 else llr
+    code = polar.polar_code_create(32768, 29492, mask)
+    polar.polar_code_compile(code, i8, 4096)
+    got = decode(code, y, i8)
+    sample = np.sort(np.random.default_rng(5).choice(4096, 40, replace=False))
+    assert np.array_equal(got[sample], oracle.decode_batch(mask, y, frames=sample))
+    polar.polar_code_compile(code, i8, 1)
+    one = decode(code, y[:1], i8)
+    assert np.array_equal(one, oracle.decode_batch(mask, y[:1]))
+
+
+def test_release_returns_to_interpreter():
+    mask, d, llr = _cases.frames(256, 128, 3.0, 50, seed=32)
+    code = polar.polar_code_create(256, 128, mask)
+    polar.polar_code_compile(code, False, 50)
+    assert polar.polar_code_get_launch(code, False, 50)["unrolled"] == 256
+    polar.polar_code_compile(code, False, 0)
+    assert polar.polar_code_get_launch(code, False, 50)["unrolled"] == 0
+    assert np.array_equal(decode(code, llr, False), oracle.decode_batch(mask, llr))
