@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--latency-frames", type=int, default=200)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-variant", action="store_true", help="skip the other LLR type")
+    p.add_argument("--interpreter", action="store_true",
+                   help="time the operation-list interpreter instead of the specialised decoder")
     return p.parse_args()
 
 
@@ -77,13 +80,8 @@ def barrier(world):
 
 
 def max_over_ranks(world, v: float) -> float:
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1504_00353_gb300 import sharding
+    return sharding.max_over_ranks(v, device="cuda") if world > 1 else v
 
 
 # ---------------------------------------------------------------- inputs
@@ -274,6 +272,49 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# Launch shapes of the specialised decoders, chosen by measurement on GB300
+# (threads per CTA, largest shared-memory alpha stage, warp-run threshold,
+# channel staging: 2 = read in place).
+TUNED = {
+    ("n32768_k29492_4.0db", "f32"): dict(threads=128, smem_stage_max=2048, warp_stage_max=512,
+                                         stage_channel=2),
+    ("n32768_k29492_4.0db", "i8"): dict(threads=128, smem_stage_max=2048, warp_stage_max=512,
+                                        stage_channel=2),
+}
+
+
+def element_ops(code):
+    """F/G/Combine/node element operations of one frame (roofline ALU count)."""
+    from paper_1504_00353_gb300 import polar
+    n = 0
+    for kind, nv, _ in polar.polar_code_schedule(code):
+        n += nv // 2 if kind in ("F", "G", "G_0R", "Combine", "Combine_0R") else nv
+    return n
+
+
+def device_timed(torch, stream, fn, steps, warmup, world):
+    """Warm-up, then `steps` back-to-back launches bracketed by barrier + sync;
+    returns (total ms max over ranks, mean per-launch ms)."""
+    for _ in range(warmup):
+        fn(0)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        fn(i)
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    return max_over_ranks(world, t0.elapsed_time(t1)), statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
 def run_native(args, world, rank, local):
     import torch
 
@@ -282,61 +323,68 @@ def run_native(args, world, rank, local):
     wl = dict(synth.WORKLOADS[args.workload])
     N, K = wl["N"], wl["K"]
     batch = args.batch or wl["n_frames"]
-    i8 = args.dtype == "i8"
-    es = 1 if i8 else 4
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-
-    mask, code, d, llr = make_inputs(wl, batch, wl["seed"] + 1000 * rank, args.dtype)
-    decode = polar.polar_decode_i8 if i8 else polar.polar_decode
-    in_bytes = batch * N * es
-    # Enough distinct input buffers that successive steps never find their
-    # input in L2 (each step streams more than L2 before a buffer is reused).
-    n_buf = 1 if in_bytes > 2 * L2_BYTES else int(np.ceil(3 * L2_BYTES / in_bytes)) + 1
-    base = torch.from_numpy(llr).to(dev)
-    bufs = [base] + [base[torch.randperm(batch, generator=torch.Generator().manual_seed(i))
-                          .to(dev)].contiguous() for i in range(1, n_buf)]
-    out = torch.empty((batch, (K + 7) // 8), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    row = (K + 7) // 8
 
-    # correctness gate against the known transmitted bits (not a parity test)
-    decode(code, bufs[0], out)
-    torch.cuda.synchronize()
-    polar.polar_code_check(code)
-    fer = float((out.cpu().numpy() != synth.pack_bits(d)).any(axis=1).mean())
+    mask, code0, d, llr32 = make_inputs(wl, batch, wl["seed"] + 1000 * rank, "f32")
+    llr_by_dtype = {"f32": llr32, "i8": synth.quantize_i8(llr32)}
 
-    for i in range(args.warmup):
-        decode(code, bufs[i % n_buf], out)
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        t_start.record(stream)
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            decode(code, bufs[i % n_buf], out)
-            ev[i][1].record(stream)
-        t_end.record(stream)
+    def setup(dtype):
+        """Code handle with its specialised decoder compiled (untimed set-up)."""
+        i8 = dtype == "i8"
+        code = polar.polar_code_create(N, K, mask)
+        shape = TUNED.get((args.workload, dtype))
+        if shape:
+            polar.polar_code_set_launch(code, i8, **shape)
+        if not args.interpreter:
+            polar.polar_code_compile(code, i8, batch)
+        return code
+
+    def throughput(dtype, steps, warmup):
+        i8 = dtype == "i8"
+        es = 1 if i8 else 4
+        code = setup(dtype)
+        decode = polar.polar_decode_i8 if i8 else polar.polar_decode
+        in_bytes = batch * N * es
+        # Enough distinct input buffers that a step never finds its input in L2
+        # (each step streams more than L2 before a buffer is reused).
+        n_buf = 1 if in_bytes > 2 * L2_BYTES else int(np.ceil(3 * L2_BYTES / in_bytes)) + 1
+        base = torch.from_numpy(llr_by_dtype[dtype]).to(dev)
+        bufs = [base] + [base[torch.randperm(batch, generator=torch.Generator().manual_seed(i))
+                              .to(dev)].contiguous() for i in range(1, n_buf)]
+        out = torch.empty((batch, row), dtype=torch.uint8, device=dev)
+        # sanity gate against the transmitted bits (not a parity test)
+        decode(code, bufs[0], out)
         torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
-    polar.polar_code_check(code)
-    elapsed_ms = max_over_ranks(world, t_start.elapsed_time(t_end))
-    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    value = world * batch * K * args.steps / (elapsed_ms * 1e-3) / 1e9
+        polar.polar_code_check(code)
+        fer = float((out.cpu().numpy() != synth.pack_bits(d)).any(axis=1).mean())
+        total_ms, launch_ms = device_timed(torch, stream, lambda i: decode(code, bufs[i % n_buf], out),
+                                           steps, warmup, world)
+        polar.polar_code_check(code)
+        return dict(code=code, decode=decode, bufs=bufs, out=out, n_buf=n_buf, in_bytes=in_bytes,
+                    total_ms=total_ms, launch_ms=launch_ms, fer=fer,
+                    gbps=world * batch * K * steps / (total_ms * 1e-3) / 1e9,
+                    launch=polar.polar_code_get_launch(code, i8, batch))
+
+    main = args.dtype
+    other = "i8" if main == "f32" else "f32"
+    with ClockSampler(local) as clk:
+        r = throughput(main, args.steps, args.warmup)
+    clocks = clk.summary()
+    alt = None if args.no_variant else throughput(other, max(3, args.steps // 2), 3)
 
     # end to end: pinned host LLRs -> device -> decode -> packed bits back to host,
     # chunked over two streams so copies overlap decoding
-    host_in = torch.from_numpy(llr).pin_memory()
-    host_out = torch.empty((batch, (K + 7) // 8), dtype=torch.uint8).pin_memory()
+    code, decode = r["code"], r["decode"]
+    host_in = torch.from_numpy(llr_by_dtype[main]).pin_memory()
+    host_out = torch.empty((batch, row), dtype=torch.uint8).pin_memory()
     chunks = 4
     cs = (batch + chunks - 1) // chunks
     streams = [torch.cuda.Stream(dev) for _ in range(2)]
-    dbuf = torch.empty_like(base)
+    dbuf = torch.empty_like(r["bufs"][0])
+    out = r["out"]
 
     def e2e_step():
         for c in range(chunks):
@@ -361,71 +409,97 @@ def run_native(args, world, rank, local):
         e2e_s = max_over_ranks(world, time.perf_counter() - t0)
         e2e_gbps = world * batch * K * e2e_steps / e2e_s / 1e9
 
-    # batch-1 frame latency (device, and with the frame's copies)
-    lat_dev, lat_e2e = [], []
+    # batch-1 frame latency, with the decoder specialised for single frames:
+    # device time (the launch queued behind a spin so host overhead is not
+    # counted) and end to end (copy in, decode, copy out, host clock)
+    lat = None
     nlat = min(args.latency_frames, batch)
-    one_in = torch.empty((1, N), dtype=base.dtype, device=dev)
-    one_out = torch.empty((1, (K + 7) // 8), dtype=torch.uint8, device=dev)
-    h1 = torch.empty((1, (K + 7) // 8), dtype=torch.uint8).pin_memory()
-    for f in range(nlat + 5 if nlat else 0):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        one_in.copy_(bufs[0][f % batch: f % batch + 1])
-        torch.cuda.synchronize()
-        a.record(stream)
-        decode(code, one_in, one_out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        one_in.copy_(host_in[f % batch: f % batch + 1], non_blocking=True)
-        decode(code, one_in, one_out)
-        h1.copy_(one_out, non_blocking=True)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        if f >= 5:
-            lat_dev.append(a.elapsed_time(b) * 1e3)
-            lat_e2e.append((t1 - t0) * 1e6)
+    if nlat:
+        i8 = main == "i8"
+        lcode = polar.polar_code_create(N, K, mask)
+        if not args.interpreter:
+            polar.polar_code_compile(lcode, i8, 1)
+        one_in = torch.empty((1, N), dtype=r["bufs"][0].dtype, device=dev)
+        one_out = torch.empty((1, row), dtype=torch.uint8, device=dev)
+        h1 = torch.empty((1, row), dtype=torch.uint8).pin_memory()
+        lat_dev, lat_e2e = [], []
+        for f in range(nlat + 5):
+            one_in.copy_(r["bufs"][0][f % batch: f % batch + 1])
+            torch.cuda.synchronize()
+            torch.cuda._sleep(1_000_000)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            decode(lcode, one_in, one_out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            one_in.copy_(host_in[f % batch: f % batch + 1], non_blocking=True)
+            decode(lcode, one_in, one_out)
+            h1.copy_(one_out, non_blocking=True)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if f >= 5:
+                lat_dev.append(a.elapsed_time(b) * 1e3)
+                lat_e2e.append((t1 - t0) * 1e6)
+        lat = {"batch": 1, "frames": nlat,
+               "device_p50": float(np.percentile(lat_dev, 50)),
+               "device_p99": float(np.percentile(lat_dev, 99)),
+               "e2e_p50": float(np.percentile(lat_e2e, 50)),
+               "e2e_p99": float(np.percentile(lat_e2e, 99)),
+               "launch": polar.polar_code_get_launch(lcode, i8, 1)}
 
     hbm_peak, peak_kind = peaks()
-    alg_bytes = batch * (N * es + (K + 7) // 8)
-    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    traffic = profile_traffic(args.workload, args.dtype)
+    es = 1 if main == "i8" else 4
+    alg_bytes = batch * (N * es + row)
+    achieved = alg_bytes / (r["launch_ms"] * 1e-3) / 1e9
+    ops = element_ops(code) * batch
+    alu_peak = 152 * 128 * 2.07e9  # lanes x max SM clock: one element-op per lane per clock
+    t_hbm = alg_bytes / (hbm_peak * 1e9)
+    t_alu = ops / alu_peak
     line = {
-        "metric": METRIC, "value": value, "unit": "Gbps", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "metric": METRIC, "value": r["gbps"], "unit": "Gbps", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": (value / PAPER_GBPS[(args.workload, args.dtype)]
-                        if (args.workload, args.dtype) in PAPER_GBPS else None),
-        "dtype": args.dtype, "data": "synthetic",
+        "vs_baseline": (r["gbps"] / PAPER_GBPS[(args.workload, main)]
+                        if (args.workload, main) in PAPER_GBPS else None),
+        "dtype": main, "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "K": K, "global_batch": batch * world,
-                   "batch_per_gpu": batch, "ebn0_db": wl["ebn0_db"], "llr": args.dtype,
+                   "batch_per_gpu": batch, "ebn0_db": wl["ebn0_db"], "llr": main,
                    "parallelism": f"frames sharded over {world} GPU(s), no collective",
-                   "l2": (f"{n_buf} distinct input buffers of {in_bytes / 2**20:.0f} MiB "
+                   "l2": (f"{r['n_buf']} distinct input buffer(s) of {r['in_bytes'] / 2**20:.0f} MiB "
                           "rotated; inputs larger than L2"),
-                   "launch": polar.polar_code_get_launch(code, i8, batch),
-                   "fer_check": fer},
-        "latency_us": ({"batch": 1, "frames": nlat,
-                        "device_p50": float(np.percentile(lat_dev, 50)),
-                        "device_p99": float(np.percentile(lat_dev, 99)),
-                        "e2e_p50": float(np.percentile(lat_e2e, 50)),
-                        "e2e_p99": float(np.percentile(lat_e2e, 99))} if nlat else None),
+                   "decoder": "interpreter" if args.interpreter else "specialised (NVRTC)",
+                   "launch": r["launch"], "fer_check": r["fer"]},
+        "latency_us": lat,
         "e2e": {"value": e2e_gbps, "unit": "Gbps",
                 "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
                 "d2h_bytes_per_step": int(host_out.numel())},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": traffic,
+        "roofline": {"bound": "hbm" if t_hbm >= t_alu else "alu",
+                     "achieved": achieved if t_hbm >= t_alu else ops / (r["launch_ms"] * 1e-3) / 1e12,
+                     "peak": hbm_peak if t_hbm >= t_alu else alu_peak / 1e12,
+                     "unit": "GB/s" if t_hbm >= t_alu else "Tops/s",
+                     "frac": (t_hbm if t_hbm >= t_alu else t_alu) / (r["launch_ms"] * 1e-3),
+                     "peak_kind": peak_kind,
+                     "traffic": profile_traffic(args.workload, main),
                      "algorithmic_bytes_per_launch": alg_bytes,
-                     "launch_ms": launch_ms},
-        "clocks": clk.summary(),
+                     "element_ops_per_launch": ops,
+                     "hbm_frac": t_hbm / (r["launch_ms"] * 1e-3),
+                     "alu_frac": t_alu / (r["launch_ms"] * 1e-3),
+                     "launch_ms": r["launch_ms"]},
+        "clocks": clocks,
     }
+    if alt:
+        line["variants"] = {other: {"value": alt["gbps"], "unit": "Gbps",
+                                    "ms_per_step": alt["total_ms"] / max(3, args.steps // 2),
+                                    "launch": alt["launch"], "fer_check": alt["fer"]}}
     if rank == 0 and not args.no_cpu_baseline:
-        f, s, T = time_oracle(mask, llr)
-        line["cpu_baseline"] = {"value": K * f / s / 1e9, "unit": "Gbps", "cores": T,
+        f, s_, T = time_oracle(mask, llr_by_dtype[main])
+        line["cpu_baseline"] = {"value": K * f / s_ / 1e9, "unit": "Gbps", "cores": T,
                                 "kind": "oracle",
-                                "sample": f"{f} frames of {args.workload} ({args.dtype}), "
+                                "sample": f"{f} frames of {args.workload} ({main}), "
                                           f"plain C Fast-SSC oracle, {T} host threads, "
-                                          f"{s:.1f} s wall"}
+                                          f"{s_:.1f} s wall"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -126,15 +126,18 @@ polar_status choose_shape(const polar_code *c, bool is_i8, size_t n_frames, int 
     const uint32_t N = c->N;
     const bool latency = n_frames * 2 <= static_cast<size_t>(dp.sms);
 
+    // Throughput: many small CTAs per SM (the serial part of a frame runs on one
+    // warp, so resident frames, not threads per frame, set the rate).
+    // Latency: one CTA with every stage in shared memory.
     uint32_t T = u.threads;
     if (!T) {
         if (latency) T = N >= 8192 ? 1024 : std::max<uint32_t>(64, pow2_floor(std::max<uint32_t>(N / 8, 32)));
-        else T = N <= 2048 ? 128 : (N <= 8192 ? 256 : 512);
+        else T = 128;
     }
     T = std::min<uint32_t>(std::max<uint32_t>(T, 32), 1024);
 
     const bool can_stage = (size_t(N) * es) % 16 == 0;
-    const size_t budget = latency ? dp.smem_optin : std::min<size_t>(dp.smem_optin, 112 * 1024);
+    const size_t budget = latency ? dp.smem_optin : std::min<size_t>(dp.smem_optin, 24 * 1024);
     uint32_t S = u.smem_stage_max ? std::max<uint32_t>(u.smem_stage_max, 64) : 0;
     if (!S) {
         S = std::max<uint32_t>(N / 2, 1);
