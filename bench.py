@@ -162,10 +162,10 @@ class ClockSampler:
 # ---------------------------------------------------------------- roofline inputs
 
 def profile_traffic(workload, dtype):
-    """DRAM bytes per launch from the committed ncu summary, when it was taken on
-    the current kernel source (its sha256 prefix is recorded beside the number)."""
-    path = os.path.join(ROOT, "profiles", f"fastssc_decode_{dtype}_{workload}.md")
-    src = os.path.join(ROOT, "paper_1504_00353_gb300", "csrc", "polar_kernels.cu")
+    """DRAM bytes per launch from the committed ncu summary of the specialised
+    decoder, when it was taken on the current decoder sources (the sha256 prefix of
+    polar_ops.cuh + polar_codegen.cpp is recorded beside the number)."""
+    path = os.path.join(ROOT, "profiles", f"fastssc_unrolled_{dtype}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -173,8 +173,10 @@ def profile_traffic(workload, dtype):
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if not cur.startswith(h.group(1)):
+    sha = hashlib.sha256()
+    for f in ("polar_ops.cuh", "polar_codegen.cpp"):
+        sha.update(open(os.path.join(ROOT, "paper_1504_00353_gb300", "csrc", f), "rb").read())
+    if not sha.hexdigest().startswith(h.group(1)):
         return None
     return float(m.group(1))
 
@@ -276,10 +278,16 @@ def run_reference(args, world, rank):
 # (threads per CTA, largest shared-memory alpha stage, warp-run threshold,
 # channel staging: 2 = read in place).
 TUNED = {
-    ("n32768_k29492_4.0db", "f32"): dict(threads=128, smem_stage_max=2048, warp_stage_max=512,
+    ("n32768_k29492_4.0db", "f32"): dict(threads=128, smem_stage_max=2048, warp_stage_max=2048,
                                          stage_channel=2),
-    ("n32768_k29492_4.0db", "i8"): dict(threads=128, smem_stage_max=2048, warp_stage_max=512,
+    ("n32768_k29492_4.0db", "i8"): dict(threads=128, smem_stage_max=4096, warp_stage_max=2048,
                                         stage_channel=2),
+    ("n1024_k512_2.5db", "f32"): dict(threads=32, stage_channel=2),
+    ("n1024_k512_2.5db", "i8"): dict(threads=32, stage_channel=2),
+}
+# Batch-1 (latency) shapes: one CTA, every stage in shared memory.
+TUNED_LATENCY = {
+    "n32768_k29492_4.0db": dict(threads=256, warp_stage_max=1024),
 }
 
 
@@ -417,6 +425,8 @@ def run_native(args, world, rank, local):
     if nlat:
         i8 = main == "i8"
         lcode = polar.polar_code_create(N, K, mask)
+        if args.workload in TUNED_LATENCY:
+            polar.polar_code_set_launch(lcode, i8, **TUNED_LATENCY[args.workload])
         if not args.interpreter:
             polar.polar_code_compile(lcode, i8, 1)
         one_in = torch.empty((1, N), dtype=r["bufs"][0].dtype, device=dev)
