@@ -129,6 +129,31 @@ polar_status polar_decode(const polar_code_t *code, const float *llr, uint8_t *b
 polar_status polar_decode_i8(const polar_code_t *code, const int8_t *llr,
                              uint8_t *bits_out, size_t n_frames, polar_stream_t stream);
 
+/* As polar_decode (float32 LLRs), for callers that cannot allocate device
+ * memory: code that runs where cudaMalloc / cudaMallocAsync are unavailable or
+ * forbidden (inside a host callback, under an allocator that must not grow,
+ * in a process whose memory budget is fixed up front). No device memory is
+ * allocated and nothing is freed; the paper has no counterpart of this call.
+ *   Scratch: the alpha stages that do not fit in shared memory go to one
+ *   static device array of 32 MiB, which every GPU that loads this library
+ *   holds until the process exits. The grid is reduced so that the resident
+ *   CTAs' stages fit in it. A launch shape whose single CTA would need more
+ *   than 32 MiB is rejected with POLAR_EINVAL; with N <= 2^20 one CTA needs
+ *   at most 4 MiB, so every valid code runs. Nothing in the array needs to
+ *   start at zero (every stage is written before it is read).
+ *   Sharing: all calls on a device use the same array, so calls whose kernels
+ *   overlap on the GPU (two streams, or two host threads) race on it; order
+ *   them on one stream or synchronise between them.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture. The handle's device tables must already be on
+ *   the current device (polar_code_create uploads them to the device current
+ *   at creation); otherwise POLAR_EINVAL, since uploading would allocate.
+ * Always runs the operation-list interpreter, with the handle's launch shape.
+ * Results are identical to polar_decode's. */
+polar_status polar_decode_noalloc(const polar_code_t *code, const float *llr,
+                                  uint8_t *bits_out, size_t n_frames, polar_stream_t stream);
+
 /* Number of float values one frame writes to a trace (the summed N_v/2 of
  * every F, G and G_0R operation). */
 size_t polar_code_trace_len(const polar_code_t *code);

@@ -432,6 +432,76 @@ polar_status polar_decode(const polar_code_t *code, const float *llr, uint8_t *b
     return decode_impl(code, llr, false, bits_out, nullptr, n_frames, stream);
 }
 
+polar_status polar_decode_noalloc(const polar_code_t *code, const float *llr, uint8_t *bits_out,
+                                  size_t n_frames, polar_stream_t stream) {
+    if (!code) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!llr || (!bits_out && code->K > 0)) return POLAR_EINVAL;
+    if (reinterpret_cast<uintptr_t>(llr) % 16 != 0) return POLAR_EALIGN;
+    if (code->K == 0) return POLAR_OK;
+    polar_code *c = const_cast<polar_code *>(code);
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    if (device < 0 || static_cast<size_t>(device) >= c->dev.size()) return POLAR_ECUDA;
+    DeviceState *ds = nullptr;
+    {
+        // the per-device tables must already exist: uploading them would allocate
+        std::lock_guard<std::mutex> g(c->mu);
+        if (!c->dev[device].ready) return POLAR_EINVAL;
+        ds = &c->dev[device];
+    }
+    LaunchShape sh{};
+    polar_status st = choose_shape(c, false, n_frames, device, &sh);
+    if (st != POLAR_OK) return st;
+    st = finish_grid(c, false, n_frames, device,
+                     occupancy(device, false, sh.stage_channel != 0, sh.threads, sh.smem_bytes), &sh);
+    if (st != POLAR_OK) return st;
+    void *scratch = nullptr;
+    const size_t per_cta = sh.scratch_elems_per_cta * 4;
+    if (per_cta) {
+        if (per_cta > kNoAllocScratchBytes) return POLAR_EINVAL;  // one CTA needs more than the array
+        sh.grid = static_cast<uint32_t>(std::min<size_t>(sh.grid, kNoAllocScratchBytes / per_cta));
+        if (noalloc_scratch(&scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return POLAR_ECUDA;
+        }
+    }
+    const size_t nops = c->ops.size();
+    KernelArgs a{};
+    a.ops = ds->tables;
+    a.trace_offs = ds->tables + nops;
+    a.ext_mask = ds->tables + 2 * nops;
+    a.ext_pre = ds->tables + 2 * nops + c->NW;
+    a.ext_wstart = ds->tables + 2 * nops + 2 * c->NW;
+    a.status = ds->status;
+    a.llr = llr;
+    a.out = bits_out;
+    a.trace = nullptr;
+    a.gscratch = scratch;
+    a.n_frames = n_frames;
+    a.trace_stride = c->trace_len;
+    a.gstride = sh.scratch_elems_per_cta;
+    a.n_ops = static_cast<uint32_t>(nops);
+    a.N = c->N;
+    a.log2N = c->log2N;
+    a.K = c->K;
+    a.S = sh.smem_stage_max;
+    a.log2W = static_cast<uint32_t>(log2u(sh.warp_stage_max));
+    a.NW = c->NW;
+    a.KW = c->KW;
+    a.out_row = (c->K + 7) / 8;
+    const cudaError_t e = launch_decode(false, false, sh.stage_channel != 0, sh, a,
+                                        reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    return POLAR_OK;
+}
+
 polar_status polar_decode_i8(const polar_code_t *code, const int8_t *llr, uint8_t *bits_out,
                              size_t n_frames, polar_stream_t stream) {
     return decode_impl(code, llr, true, bits_out, nullptr, n_frames, stream);

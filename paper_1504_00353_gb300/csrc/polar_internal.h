@@ -78,6 +78,13 @@ int kernel_max_ctas_per_sm(bool is_i8, bool stage_channel, uint32_t threads,
 // Raise a kernel's dynamic shared-memory limit to the device maximum (once).
 cudaError_t ensure_smem_limit(const void *k);
 
+// Size of the static device scratch used by polar_decode_noalloc (per device).
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+
+// Device address of that scratch on the current device; the first call on a
+// device looks it up with cudaGetSymbolAddress (no allocation).
+cudaError_t noalloc_scratch(void **ptr);
+
 // Launch the interpreter kernel. Returns the CUDA error of the launch.
 cudaError_t launch_decode(bool is_i8, bool trace, bool stage_channel,
                           const LaunchShape &shape, const KernelArgs &args,

@@ -281,6 +281,32 @@ cudaError_t ensure_smem_limit(const void *k) {
 }
 
 
+// Fixed device scratch for polar_decode_noalloc: the alpha stages above the
+// shared-memory cap of every resident CTA live here instead of in memory taken
+// with cudaMallocAsync. Every GPU that loads this library holds the array until
+// the process exits; all calls on a device share it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t noalloc_scratch(void **ptr) {
+    static std::mutex mu;
+    static void *addr[kMaxDevices] = {};
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || static_cast<size_t>(device) >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[device]) {
+        // Host code only knows a stand-in for the array; its device address is
+        // looked up once per device, with that device current.
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[device] = p;
+    }
+    *ptr = addr[device];
+    return cudaSuccess;
+}
+
 size_t kernel_smem_bytes(uint32_t N, uint32_t S, uint32_t threads, bool is_i8, bool stage) {
     (void)threads;
     return SmemLayout(N, S, is_i8 ? 1u : 4u, stage).total;

@@ -25,6 +25,7 @@ EXPORTS = [
     "polar_code_info", "polar_code_schedule", "polar_encode_systematic", "polar_decode",
     "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
     "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_log",
+    "polar_decode_noalloc",
 ]
 
 
@@ -54,6 +55,7 @@ def _load():
         "polar_encode_systematic": ([vp, u8p, u8p, sz], st),
         "polar_decode": ([vp, vp, vp, sz, vp], st),
         "polar_decode_i8": ([vp, vp, vp, sz, vp], st),
+        "polar_decode_noalloc": ([vp, vp, vp, sz, vp], st),
         "polar_code_trace_len": ([vp], sz),
         "polar_decode_trace": ([vp, vp, st, vp, vp, sz, vp], st),
         "polar_code_set_launch": ([vp, st, u32, u32, u32, u32, u32], st),
@@ -193,6 +195,16 @@ def polar_decode(code: PolarCode, llr, bits_out=None, n_frames=None, stream=None
     import torch
     return _decode(_lib.polar_decode, "polar_decode", code, llr, bits_out, n_frames, stream,
                    torch.float32)
+
+
+def polar_decode_noalloc(code: PolarCode, llr, bits_out, n_frames=None, stream=None):
+    """polar_decode without device allocation (static device scratch); bits_out is
+    required, since creating it would allocate."""
+    import torch
+    if bits_out is None:
+        raise ValueError("polar_decode_noalloc: bits_out must be provided")
+    return _decode(_lib.polar_decode_noalloc, "polar_decode_noalloc", code, llr, bits_out,
+                   n_frames, stream, torch.float32)
 
 
 def polar_decode_i8(code: PolarCode, llr, bits_out=None, n_frames=None, stream=None):
