@@ -217,6 +217,54 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
  * until the next compile or destroy). */
 const char *polar_code_compile_log(const polar_code_t *code);
 
+/* ---- Mixed-code batches: one persistent launch over frames of several codes ---- */
+
+typedef struct polar_batch polar_batch_t;
+
+/* Build a decoder for frames that belong to any of n_codes codes (1..64),
+ * all of one LLR type (is_i8 = 0 float32, 1 int8). One kernel is generated
+ * and compiled with NVRTC holding the decoder specialised to each code
+ * (Sec. III-B, "Unrolled Decoder"); its CTAs claim frames from a work queue
+ * with an atomic counter, so frames of different lengths balance across the
+ * GPU in a single launch.
+ *   codes           handles created with the current device current; they
+ *                   must outlive the batch decoder.
+ *   threads         threads per CTA (multiple of 32; 0 = 32: one warp per
+ *                   frame, the shape that measured fastest for int8).
+ *   smem_stage_max  per code, the largest alpha stage kept in shared memory
+ *                   (power of two; NULL or 0 entries = 512 for 32 threads,
+ *                   2048 otherwise). Larger stages use device scratch.
+ * The descriptor table, the work counter and the scratch of every resident
+ * CTA are allocated here, so polar_batch_decode allocates nothing and can be
+ * captured in a CUDA graph. Blocking (NVRTC compile). */
+polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
+                                uint32_t threads, const uint32_t *smem_stage_max,
+                                polar_batch_t **out);
+
+void polar_batch_destroy(polar_batch_t *batch);
+
+/* Decode n_frames frames in one launch on `stream`. All arrays are device
+ * memory owned by the caller:
+ *   code_id[i]  index (into the codes given at creation) of frame i's code;
+ *   llr_off[i]  element offset of frame i's N LLRs in `llr` (16-byte aligned
+ *               frame start: a multiple of 4 for float32, 16 for int8);
+ *   out_off[i]  byte offset of frame i's ceil(K/8) output bytes in bits_out.
+ * Frames are claimed in index order, so listing the longest codes first gives
+ * the best balance. Calls on one batch decoder share its work counter and
+ * scratch: they must not overlap on the GPU (issue them on one stream). */
+polar_status polar_batch_decode(polar_batch_t *batch, const uint32_t *code_id,
+                                const uint64_t *llr_off, const uint64_t *out_off,
+                                const void *llr, uint8_t *bits_out, size_t n_frames,
+                                polar_stream_t stream);
+
+/* Launch shape of the batch decoder (non-NULL pointers are written). */
+polar_status polar_batch_info(const polar_batch_t *batch, uint32_t *threads, uint32_t *grid,
+                              size_t *smem_bytes, size_t *scratch_bytes);
+
+/* NVRTC log of the batch decoder's compilation (never NULL). With batch =
+ * NULL: the log of the last polar_batch_create that failed on this thread. */
+const char *polar_batch_log(const polar_batch_t *batch);
+
 /* Wait for `stream`, then read and clear the handle's device status word on
  * the current device. POLAR_ETIMEOUT if a bounded device wait expired since
  * the last check, POLAR_OK otherwise. */

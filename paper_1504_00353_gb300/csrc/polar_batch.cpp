@@ -1,0 +1,214 @@
+// Mixed-code batches: one persistent kernel decodes frames of several polar
+// codes from a work queue, each frame with the decoder body specialised to its
+// code (polar_codegen.cpp). Everything the launch needs (descriptor table,
+// work counter, alpha scratch for the resident CTAs) is allocated when the
+// batch decoder is created, so a decode call allocates nothing and a stream
+// that issues it can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "polar_gb300.h"
+#include "polar_internal.h"
+
+using namespace polar;
+
+struct polar_batch {
+    bool is_i8 = false;
+    int device = -1;
+    uint32_t threads = 32;
+    std::vector<polar_code *> codes;
+    std::vector<uint32_t> S, W, R;
+    CompiledKernel ck;
+    LaunchShape shape{};
+    CodeDesc *d_codes = nullptr;
+    unsigned int *d_counter = nullptr;
+    void *scratch = nullptr;
+    size_t gstride = 0;
+    uint32_t alpha_elems = 0, beta_words = 0;
+    std::string log;
+
+    ~polar_batch() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (device >= 0) cudaSetDevice(device);
+        cudaFree(d_codes);
+        cudaFree(d_counter);
+        cudaFree(scratch);
+        if (ck.lib) cudaLibraryUnload(ck.lib);
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+};
+
+namespace {
+
+// Log of the last polar_batch_create that failed on this thread.
+thread_local std::string g_failed_log;
+
+polar_status st_of(cudaError_t e) {
+    if (e == cudaSuccess) return POLAR_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
+                                uint32_t threads, const uint32_t *smem_stage_max,
+                                polar_batch_t **out) {
+    if (!codes || !out || n_codes == 0 || n_codes > 64) return POLAR_EINVAL;
+    if (threads == 0) threads = 32;
+    if (threads % 32 || threads > 1024) return POLAR_EINVAL;
+    for (uint32_t c = 0; c < n_codes; ++c)
+        if (!codes[c]) return POLAR_EINVAL;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    polar_batch *b = new (std::nothrow) polar_batch;
+    if (!b) return POLAR_ENOMEM;
+    b->is_i8 = is_i8 != 0;
+    b->device = device;
+    b->threads = threads;
+    const uint32_t es = b->is_i8 ? 1 : 4;
+    std::vector<CodeDesc> desc(n_codes);
+    std::vector<const polar_code *> cc;
+    for (uint32_t c = 0; c < n_codes; ++c) {
+        polar_code *code = codes[c];
+        uint32_t s = smem_stage_max && smem_stage_max[c] ? smem_stage_max[c]
+                                                         : (threads == 32 ? 512u : 2048u);
+        if (!is_pow2(s)) {
+            delete b;
+            return POLAR_EINVAL;
+        }
+        s = std::min<uint32_t>(std::max<uint32_t>(s, 64), std::max<uint32_t>(code->N / 2, 1));
+        b->codes.push_back(code);
+        b->S.push_back(s);
+        b->W.push_back(std::max<uint32_t>(2048, 256));
+        b->R.push_back(256);
+        cc.push_back(code);
+        b->alpha_elems = std::max(b->alpha_elems, 2 * s);
+        b->beta_words = std::max(b->beta_words, code->NW);
+        const size_t g = (code->N / 2 > s) ? size_t(code->N) - 2 * size_t(s) : 0;
+        b->gstride = std::max(b->gstride, g ? ((g * es + 15) / 16 * 16) / es : size_t(0));
+    }
+    // device tables of every code
+    for (uint32_t c = 0; c < n_codes; ++c) {
+        polar_code *code = b->codes[c];
+        std::lock_guard<std::mutex> g(code->mu);
+        if (!code->dev[device].ready) {
+            delete b;
+            return POLAR_EINVAL;  // create the codes with this device current
+        }
+        const DeviceState &ds = code->dev[device];
+        const size_t nops = code->ops.size();
+        desc[c].ext_mask = ds.tables + 2 * nops;
+        desc[c].ext_pre = ds.tables + 2 * nops + code->NW;
+        desc[c].ext_wstart = ds.tables + 2 * nops + 2 * code->NW;
+        desc[c].N = code->N;
+        desc[c].K = code->K;
+        desc[c].NW = code->NW;
+        desc[c].KW = code->KW;
+        desc[c].out_row = (code->K + 7) / 8;
+        desc[c].S = b->S[c];
+    }
+    const size_t smem = align_up(size_t(b->alpha_elems) * es, 128) +
+                        align_up(size_t(b->beta_words) * 4, 16) + 32 * 8 + 32 * 4;
+    int optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (smem > size_t(optin) || sms <= 0) {
+        delete b;
+        return POLAR_EINVAL;
+    }
+    const uint32_t min_blocks = static_cast<uint32_t>(std::max<size_t>(
+        1, std::min<size_t>({size_t(228 * 1024) / (smem + 1024), size_t(2048 / threads), size_t(32)})));
+    const std::string src = generate_batch_source(cc, b->is_i8, b->S, b->W, b->R, threads, min_blocks);
+    cudaError_t e = compile_source(src, &b->ck, &b->log, "polar_batch");
+    if (e != cudaSuccess) {
+        const polar_status st = st_of(e);
+        g_failed_log = b->log + "\n(compile status " + std::to_string(static_cast<int>(e)) + ")";
+        delete b;
+        return st;
+    }
+    const int occ = compiled_max_ctas(&b->ck, threads, smem);
+    if (occ <= 0) {
+        g_failed_log = b->log + "\nno CTA of this shape can be resident (smem " +
+                       std::to_string(smem) + " bytes, " + std::to_string(threads) + " threads)";
+        delete b;
+        return POLAR_ECUDA;
+    }
+    b->shape.threads = threads;
+    b->shape.smem_bytes = smem;
+    b->shape.grid = static_cast<uint32_t>(sms * occ);
+    b->shape.ctas_per_sm = static_cast<uint32_t>(occ);
+    b->shape.scratch_elems_per_cta = b->gstride;
+    e = cudaMalloc(&b->d_codes, sizeof(CodeDesc) * n_codes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_codes, desc.data(), sizeof(CodeDesc) * n_codes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned int));
+    if (e == cudaSuccess && b->gstride)
+        e = cudaMalloc(&b->scratch, size_t(b->shape.grid) * b->gstride * es);
+    if (e != cudaSuccess) {
+        const polar_status st = st_of(e);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return POLAR_OK;
+}
+
+void polar_batch_destroy(polar_batch_t *batch) { delete batch; }
+
+polar_status polar_batch_decode(polar_batch_t *b, const uint32_t *code_id, const uint64_t *llr_off,
+                                const uint64_t *out_off, const void *llr, uint8_t *bits_out,
+                                size_t n_frames, polar_stream_t stream) {
+    if (!b) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!code_id || !llr_off || !out_off || !llr || !bits_out) return POLAR_EINVAL;
+    if (reinterpret_cast<uintptr_t>(llr) % 16 != 0) return POLAR_EALIGN;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess || device != b->device) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return st_of(e);
+    BatchArgs a{};
+    a.codes = b->d_codes;
+    a.code_id = code_id;
+    a.llr_off = reinterpret_cast<const unsigned long long *>(llr_off);
+    a.out_off = reinterpret_cast<const unsigned long long *>(out_off);
+    a.llr = llr;
+    a.out = bits_out;
+    a.counter = b->d_counter;
+    a.gscratch = b->scratch;
+    a.gstride = b->gstride;
+    a.n_frames = n_frames;
+    a.smem_alpha_elems = b->alpha_elems;
+    a.smem_beta_words = b->beta_words;
+    e = launch_compiled(&b->ck, b->shape, &a, s);
+    return st_of(e);
+}
+
+polar_status polar_batch_info(const polar_batch_t *b, uint32_t *threads, uint32_t *grid,
+                              size_t *smem_bytes, size_t *scratch_bytes) {
+    if (!b) return POLAR_EINVAL;
+    if (threads) *threads = b->shape.threads;
+    if (grid) *grid = b->shape.grid;
+    if (smem_bytes) *smem_bytes = b->shape.smem_bytes;
+    if (scratch_bytes) *scratch_bytes = size_t(b->shape.grid) * b->gstride * (b->is_i8 ? 1 : 4);
+    return POLAR_OK;
+}
+
+const char *polar_batch_log(const polar_batch_t *b) { return b ? b->log.c_str() : g_failed_log.c_str(); }
+
+}  // extern "C"

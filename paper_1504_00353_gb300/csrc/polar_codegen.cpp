@@ -115,9 +115,14 @@ CUfunction device_function(CompiledKernel *ck) {
     cudaFree(nullptr);  // make the primary context current
     CUfunction f = nullptr;
     if (drv.kernel_get_function(&f, reinterpret_cast<CUkernel>(ck->kernel)) != CUDA_SUCCESS) return nullptr;
-    int optin = 0;
+    // The dynamic limit plus the kernel's static shared memory may not exceed
+    // the opt-in maximum per block.
+    int optin = 0, static_smem = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (drv.func_set_attribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin) != CUDA_SUCCESS)
+    if (drv.func_get_attribute(&static_smem, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, f) != CUDA_SUCCESS)
+        return nullptr;
+    if (drv.func_set_attribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                               optin - static_smem) != CUDA_SUCCESS)
         return nullptr;
     ck->func[device] = f;
     return f;
@@ -130,19 +135,17 @@ const char *kind_name(uint32_t kind) {
 
 }  // namespace
 
-std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
-                            uint32_t reg_subtree) {
-    const uint32_t N = code.N;
-    const uint32_t S = shape.smem_stage_max;
-    const uint32_t W = shape.warp_stage_max;
-    const std::vector<HostOp> ops = code.build_ops(reg_subtree);
-    const char *T = is_i8 ? "int8_t" : "float";
+namespace {
 
-    std::ostringstream o;
-    o << "// Fast-SSC decoder specialised to one (" << N << ", " << code.K << ") polar code\n"
-      << "#include \"polar_ops.cuh\"\n"
-      << "namespace polar {\n"
-      << "struct GenBody {\n"
+// struct <name> { operator()(frame) }: the code's operation list with every
+// node size and offset written as a constant. S = shared-memory stage cap,
+// W = widest node run on warp 0 alone, R = largest register-resident subtree.
+void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
+               uint32_t R, const std::string &name) {
+    const uint32_t N = code.N;
+    const std::vector<HostOp> ops = code.build_ops(R);
+    const char *T = is_i8 ? "int8_t" : "float";
+    o << "struct " << name << " {\n"
       << "  __device__ __forceinline__ void operator()(const Frame<" << T << "> &fr, float *) const {\n"
       << "    using T = " << T << ";\n"
       << "    constexpr uint32_t N = " << N << "u, S = " << S << "u;\n"
@@ -159,7 +162,8 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
         s << "gen_out<T, S, " << n << "u>(fr)";
         return s.str();
     };
-    // Memory-resident operation on the whole CTA or on warp 0.
+    // Memory-resident operation on the whole CTA or on warp 0 (inlined with
+    // constant arguments: out-of-line copies measured slower).
     auto mem_op = [&](const HostOp &op, const char *grp) {
         const uint32_t n = 1u << op.log2n, off = op.off;
         switch (op.kind) {
@@ -220,7 +224,7 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
         if (op.flags & OPW_REG_ENTER) {
             o0 = op.off;
             n0 = n;
-            o << "      {\n        RegSub<T, " << reg_subtree << "u> r;\n        r.lane = lane;\n"
+            o << "      {\n        RegSub<T, " << R << "u> r;\n        r.lane = lane;\n"
               << "        r.template enter<" << n0 << "u>(" << in(n0) << ");\n";
         }
         const uint32_t p = op.off - o0;
@@ -242,15 +246,51 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
         }
     }
     if (in_run) o << "    }\n    __syncthreads();\n";
-    o << "  }\n};\n}  // namespace polar\n"
+    o << "  }\n};\n";
+}
+
+}  // namespace
+
+std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
+                            uint32_t reg_subtree) {
+    std::ostringstream o;
+    o << "// Fast-SSC decoder specialised to one (" << code.N << ", " << code.K << ") polar code\n"
+      << "#include \"polar_ops.cuh\"\n"
+      << "namespace polar {\n";
+    emit_body(o, code, is_i8, shape.smem_stage_max, shape.warp_stage_max, reg_subtree, "GenBody");
+    o << "}  // namespace polar\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << shape.threads << ", "
       << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n"
-      << "  polar::run_frames<" << T << ", false, " << (shape.stage_channel ? "true" : "false")
-      << ">(a, polar::GenBody{});\n}\n";
+      << "  polar::run_frames<" << (is_i8 ? "int8_t" : "float") << ", false, "
+      << (shape.stage_channel ? "true" : "false") << ">(a, polar::GenBody{});\n}\n";
     return o.str();
 }
 
-cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::string *log) {
+std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,
+                                  const std::vector<uint32_t> &S, const std::vector<uint32_t> &W,
+                                  const std::vector<uint32_t> &R, uint32_t threads,
+                                  uint32_t min_blocks) {
+    std::ostringstream o;
+    const char *T = is_i8 ? "int8_t" : "float";
+    o << "// Mixed-batch Fast-SSC decoder: one specialised body per code\n"
+      << "#include \"polar_ops.cuh\"\n"
+      << "namespace polar {\n";
+    for (size_t c = 0; c < codes.size(); ++c)
+        emit_body(o, *codes[c], is_i8, S[c], W[c], R[c], "Body" + std::to_string(c));
+    o << "struct BatchBody {\n"
+      << "  __device__ __forceinline__ void operator()(uint32_t cid, const Frame<" << T
+      << "> &fr) const {\n    switch (cid) {\n";
+    for (size_t c = 0; c < codes.size(); ++c)
+        o << "    case " << c << ": Body" << c << "{}(fr, nullptr); break;\n";
+    o << "    default: break;\n    }\n  }\n};\n}  // namespace polar\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
+      << std::max<uint32_t>(min_blocks, 1) << ") polar_batch(const polar::BatchArgs a) {\n"
+      << "  polar::run_batch<" << T << ">(a, polar::BatchBody{});\n}\n";
+    return o.str();
+}
+
+cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::string *log,
+                           const char *kernel_name) {
     const Nvrtc &nv = nvrtc();
     if (!nv.ok) {
         *log = "NVRTC (libnvrtc.so) could not be loaded";
@@ -277,6 +317,7 @@ cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::str
     nv.log_size(prog, &ls);
     std::string lg(ls, '\0');
     if (ls) nv.log(prog, &lg[0]);
+    lg.resize(std::strlen(lg.c_str()));  // drop the terminating NUL
     *log = lg;
     if (r != NVRTC_SUCCESS) {
         nv.destroy(&prog);
@@ -289,7 +330,7 @@ cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::str
     nv.destroy(&prog);
     e = cudaLibraryLoadData(&out->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) return e;
-    e = cudaLibraryGetKernel(&out->kernel, out->lib, "polar_unrolled");
+    e = cudaLibraryGetKernel(&out->kernel, out->lib, kernel_name);
     if (e != cudaSuccess) {
         cudaLibraryUnload(out->lib);
         out->lib = nullptr;
@@ -322,11 +363,11 @@ int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes) {
     return n;
 }
 
-cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const KernelArgs &args,
+cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const void *args,
                             cudaStream_t stream) {
     CUfunction f = device_function(ck);
     if (!f) return cudaErrorInvalidDeviceFunction;
-    void *params[] = {const_cast<KernelArgs *>(&args)};
+    void *params[] = {const_cast<void *>(args)};
     const CUresult r = driver().launch(f, shape.grid, 1, 1, shape.threads, 1, 1,
                                        static_cast<unsigned>(shape.smem_bytes),
                                        reinterpret_cast<CUstream>(stream), params, nullptr);

@@ -276,7 +276,7 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     a.gscratch = scratch;
     cudaError_t e;
     if (ck) {
-        e = launch_compiled(ck, sh, a, s);
+        e = launch_compiled(ck, sh, &a, s);
     } else {
         e = launch_decode(is_i8, trace != nullptr, sh.stage_channel != 0, sh, a, s);
     }

@@ -236,13 +236,21 @@ namespace polar {
 // Source text of the decoder specialised to `code` for one launch shape.
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
                             uint32_t reg_subtree);
+// Source of the mixed-batch decoder: one specialised body per code (per-code
+// shared-memory stage cap S, warp threshold W, register subtree R).
+std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,
+                                  const std::vector<uint32_t> &S, const std::vector<uint32_t> &W,
+                                  const std::vector<uint32_t> &R, uint32_t threads,
+                                  uint32_t min_blocks);
 // Compile generated source with NVRTC for the current device's architecture and
-// load it. Returns cudaSuccess and fills *out, or an error (log in *log).
-cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::string *log);
+// load `kernel_name` from it. Returns cudaSuccess and fills *out, or an error
+// (log in *log).
+cudaError_t compile_source(const std::string &src, CompiledKernel *out, std::string *log,
+                           const char *kernel_name = "polar_unrolled");
 // Resident CTAs per SM of a compiled decoder on the current device (0 on error);
 // also raises its dynamic shared-memory limit to the device maximum.
 int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes);
 // Launch a compiled decoder on the current device.
-cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const KernelArgs &args,
+cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const void *args,
                             cudaStream_t stream);
 }  // namespace polar

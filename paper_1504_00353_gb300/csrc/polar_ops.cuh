@@ -91,6 +91,33 @@ struct KernelArgs {
     uint32_t out_row;              // bytes per output row (ceil(K/8))
 };
 
+// One code of a mixed batch, as the batch kernel sees it.
+struct CodeDesc {
+    const uint32_t *ext_mask;      // as in KernelArgs
+    const uint32_t *ext_pre;
+    const uint32_t *ext_wstart;
+    uint32_t N, K, NW, KW, out_row;
+    uint32_t S;                    // smem_stage_max of this code (clipped to N/2)
+};
+
+// Parameters of the mixed-batch kernel: frame i belongs to code code_id[i],
+// its LLRs start at element llr_off[i] of llr, its packed bits at byte
+// out_off[i] of out. CTAs claim frames with an atomic counter.
+struct BatchArgs {
+    const CodeDesc *codes;
+    const uint32_t *code_id;
+    const unsigned long long *llr_off;
+    const unsigned long long *out_off;
+    const void *llr;
+    uint8_t *out;
+    unsigned int *counter;         // next unclaimed frame; zero before the launch
+    void *gscratch;
+    size_t gstride;                // scratch elements per CTA (max over codes)
+    size_t n_frames;
+    uint32_t smem_alpha_elems;     // alpha region: max over codes of 2 * S
+    uint32_t smem_beta_words;      // beta region: max over codes of NW
+};
+
 __host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Shared-memory carve-up, computed identically on host and device.
@@ -663,6 +690,59 @@ __device__ __forceinline__ void run_frames(const KernelArgs &a, const Body &body
             bulk_load((it & 1u) ? chan1 : chan0, llr + (f + 2 * G) * a.N, chan_bytes,
                       &mbar[it & 1u]);
         }
+    }
+}
+
+// ---------------------------------------------------------------- mixed batches
+
+// Persistent loop of the mixed-batch kernel: each CTA claims the next frame,
+// points its Frame at the frame's code (shared base pointers, per-code N and
+// S), runs `body(code_id, fr)` and packs the frame's information bits.
+template <typename T, class Body>
+__device__ __forceinline__ void run_batch(const BatchArgs &a, const Body &body) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned int s_item;
+    const uint32_t tid = threadIdx.x;
+    const size_t alpha_bytes = align_up(size_t(a.smem_alpha_elems) * sizeof(T), 128);
+    const size_t beta_bytes = align_up(size_t(a.smem_beta_words) * 4, 16);
+    Frame<T> fr;
+    fr.s_alpha = reinterpret_cast<T *>(smem);
+    fr.beta = reinterpret_cast<uint32_t *>(smem + alpha_bytes);
+    fr.rkey = reinterpret_cast<unsigned long long *>(smem + alpha_bytes + beta_bytes);
+    fr.rpar = reinterpret_cast<uint32_t *>(smem + alpha_bytes + beta_bytes + 32 * 8);
+    fr.g_alpha = a.gscratch ? static_cast<T *>(a.gscratch) + size_t(blockIdx.x) * a.gstride : nullptr;
+    const T *llr = static_cast<const T *>(a.llr);
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const size_t item = s_item;
+        __syncthreads();  // every thread has read s_item before it is overwritten
+        if (item >= a.n_frames) break;
+        const uint32_t cid = __ldg(a.code_id + item);
+        const CodeDesc d = a.codes[cid];
+        fr.N = d.N;
+        fr.S = d.S;
+        fr.chan = llr + __ldg(a.llr_off + item);
+        body(cid, fr);
+        uint8_t *out = a.out + __ldg(a.out_off + item);
+        for (uint32_t u = tid; u < d.KW; u += blockDim.x) {
+            const uint32_t lo = u << 5;
+            const uint32_t hi = min(lo + 32u, d.K);
+            uint32_t acc = 0;
+            for (uint32_t w = __ldg(d.ext_wstart + u); w < d.NW; ++w) {
+                const uint32_t pre = __ldg(d.ext_pre + w);
+                if (pre >= hi) break;
+                const uint32_t m = __ldg(d.ext_mask + w);
+                if (!m) continue;
+                const uint32_t e = pext32(fr.beta[w], m);
+                const int pos = static_cast<int>(pre) - static_cast<int>(lo);
+                acc |= pos >= 0 ? (e << pos) : (e >> (-pos));
+            }
+            if (hi - lo < 32) acc &= (1u << (hi - lo)) - 1u;
+            const uint32_t nb = min(4u, d.out_row - 4u * u);
+            for (uint32_t b = 0; b < nb; ++b) out[4u * u + b] = static_cast<uint8_t>(acc >> (8 * b));
+        }
+        __syncthreads();
     }
 }
 

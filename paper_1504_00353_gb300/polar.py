@@ -25,7 +25,8 @@ EXPORTS = [
     "polar_code_info", "polar_code_schedule", "polar_encode_systematic", "polar_decode",
     "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
     "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_log",
-    "polar_decode_noalloc",
+    "polar_decode_noalloc", "polar_batch_create", "polar_batch_destroy", "polar_batch_decode",
+    "polar_batch_info", "polar_batch_log",
 ]
 
 
@@ -63,6 +64,11 @@ def _load():
         "polar_code_compile": ([vp, st, sz, u32], st),
         "polar_code_compile_log": ([vp], ctypes.c_char_p),
         "polar_code_check": ([vp, vp], st),
+        "polar_batch_create": ([ctypes.POINTER(vp), u32, st, u32, u32p, ctypes.POINTER(vp)], st),
+        "polar_batch_destroy": ([vp], None),
+        "polar_batch_decode": ([vp, vp, vp, vp, vp, vp, sz, vp], st),
+        "polar_batch_info": ([vp, u32p, u32p, szp, szp], st),
+        "polar_batch_log": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -271,3 +277,59 @@ def polar_code_check(code: PolarCode, stream=None):
 
 def polar_status_str(status: int) -> str:
     return _lib.polar_status_str(status).decode()
+
+
+class PolarBatch:
+    """Owns a polar_batch_t (mixed-code batch decoder); keeps its codes alive."""
+
+    def __init__(self, handle: int, codes, is_i8: bool):
+        self.handle = ctypes.c_void_p(handle)
+        self.codes = list(codes)
+        self.is_i8 = is_i8
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.polar_batch_destroy(h)
+            self.handle = ctypes.c_void_p(0)
+
+
+def polar_batch_create(codes, is_i8: bool, threads: int = 0, smem_stage_max=None) -> PolarBatch:
+    arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
+    sm = None
+    if smem_stage_max is not None:
+        sm = (ctypes.c_uint32 * len(codes))(*[int(v) for v in smem_stage_max])
+    h = ctypes.c_void_p()
+    st = _lib.polar_batch_create(arr, len(codes), int(bool(is_i8)), threads, sm, ctypes.byref(h))
+    if st != 0:
+        raise PolarError(st, "polar_batch_create: " +
+                         (_lib.polar_batch_log(None) or b"").decode(errors="replace")[-3000:])
+    return PolarBatch(h.value, codes, bool(is_i8))
+
+
+def polar_batch_destroy(batch: PolarBatch):
+    batch.__del__()
+
+
+def polar_batch_decode(batch: PolarBatch, code_id, llr_off, out_off, llr, bits_out, n_frames=None,
+                       stream=None):
+    """code_id (int32/uint32), llr_off / out_off (int64) and llr / bits_out are CUDA tensors."""
+    n = code_id.numel() if n_frames is None else int(n_frames)
+    _check(_lib.polar_batch_decode(batch.handle, ctypes.c_void_p(code_id.data_ptr()),
+                                   ctypes.c_void_p(llr_off.data_ptr()),
+                                   ctypes.c_void_p(out_off.data_ptr()),
+                                   ctypes.c_void_p(llr.data_ptr()), ctypes.c_void_p(bits_out.data_ptr()),
+                                   n, _stream_handle(stream)), "polar_batch_decode")
+    return bits_out
+
+
+def polar_batch_info(batch: PolarBatch) -> dict:
+    t, g = ctypes.c_uint32(), ctypes.c_uint32()
+    sm, sc = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.polar_batch_info(batch.handle, ctypes.byref(t), ctypes.byref(g), ctypes.byref(sm),
+                                 ctypes.byref(sc)), "polar_batch_info")
+    return dict(threads=t.value, grid=g.value, smem_bytes=sm.value, scratch_bytes=sc.value)
+
+
+def polar_batch_log(batch: PolarBatch) -> str:
+    return (_lib.polar_batch_log(batch.handle) or b"").decode(errors="replace")
