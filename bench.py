@@ -56,6 +56,14 @@ def parse():
     p.add_argument("--no-variant", action="store_true", help="skip the other LLR type")
     p.add_argument("--interpreter", action="store_true",
                    help="time the operation-list interpreter instead of the specialised decoder")
+    p.add_argument("--mode", choices=["throughput", "mixed", "serve"], default="throughput",
+                   help="throughput: one code, batch and batch-1 (default); mixed: 65,536 frames "
+                        "of five codes, one persistent launch in a CUDA graph vs one launch per "
+                        "code; serve: Poisson arrivals through the serving loop vs a plain queue")
+    p.add_argument("--loads", default="1,10,50,200", help="serve: offered loads, coded Gbps")
+    p.add_argument("--serve-seconds", type=float, default=1.0,
+                   help="serve: seconds of arrivals per load (at most --serve-max-frames)")
+    p.add_argument("--serve-max-frames", type=int, default=1_000_000)
     return p.parse_args()
 
 
@@ -345,6 +353,9 @@ def run_native(args, world, rank, local):
         i8 = dtype == "i8"
         code = polar.polar_code_create(N, K, mask)
         shape = TUNED.get((args.workload, dtype))
+        tuned, src = tuned_or(N, K, mask, dtype, {})
+        if src == "tuned":  # the autotuner's table for this GPU
+            shape = dict(tuned, stage_channel=2)
         if shape:
             polar.polar_code_set_launch(code, i8, **shape)
         if not args.interpreter:
@@ -515,8 +526,322 @@ def run_native(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- mixed lengths
+
+def mixed_inputs(n, dtype, seed, ebn0=None, ebn0_range=None):
+    """n frames of codes drawn uniformly from synth.MIXED_CODES: code ids, per-code
+    frame indices, per-code LLR arrays and info bits (library host encoder)."""
+    from paper_1504_00353_gb300 import polar
+    nk = synth.MIXED_CODES
+    masks = [synth.frozen_mask(N, K, synth.MIXED_DESIGN_DB) for N, K in nk]
+    rng = np.random.default_rng(seed)
+    cid = rng.integers(0, len(nk), n)
+    llr, bits = [], []
+    for c, (N, K) in enumerate(nk):
+        m = int((cid == c).sum())
+        code = polar.polar_code_create(N, K, masks[c])
+        d = synth.info_bits(rng, m, K)
+        cw = synth.unpack_bits(polar.polar_encode_systematic(code, synth.pack_bits(d)), N)
+        if ebn0_range is None:
+            y = synth.awgn_llr(rng, cw, ebn0 if ebn0 is not None else synth.MIXED_DESIGN_DB, K / N)
+        else:
+            dbs = rng.uniform(*ebn0_range, m)
+            y = np.empty((m, N), np.float32)
+            for j in range(m):
+                y[j] = synth.awgn_llr(rng, cw[j:j + 1], dbs[j], K / N)[0]
+        llr.append(synth.quantize_i8(y) if dtype == "i8" else y)
+        bits.append(synth.pack_bits(d))
+    return masks, cid, llr, bits
+
+
+def tuned_or(N, K, mask, dtype, default):
+    from paper_1504_00353_gb300 import autotune
+    try:
+        e = autotune.lookup(N, K, mask, dtype)
+    except Exception:  # no table or no device name
+        e = None
+    if not e:
+        return dict(default), "default"
+    return {k: e[k] for k in ("threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm")}, "tuned"
+
+
+def batch_shape(dtype):
+    from paper_1504_00353_gb300 import autotune
+    try:
+        e = autotune.load_table().get(autotune.device_name(), {}).get(f"mixed_{dtype}")
+    except Exception:
+        e = None
+    if e:
+        return dict(threads=e["threads"], smem_stage_max=e["smem_stage_max"],
+                    warp_stage_max=e["warp_stage_max"]), "tuned"
+    return dict(threads=32, smem_stage_max=None, warp_stage_max=None), "default"
+
+
+def run_mixed(args):
+    """65,536 frames drawn uniformly from five codes, int8 LLRs: one persistent
+    launch of the mixed-batch decoder replayed from a CUDA graph, against one
+    launch per code (each code's frames contiguous, its own tuned decoder)."""
+    import torch
+
+    from paper_1504_00353_gb300 import polar
+    dtype = args.dtype
+    n = args.batch or synth.MIXED_FRAMES
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    nk = synth.MIXED_CODES
+    t_gen = time.perf_counter()
+    masks, cid, llr, bits = mixed_inputs(n, dtype, seed=3)
+    t_gen = time.perf_counter() - t_gen
+    es = 1 if dtype == "i8" else 4
+    info_bits = sum(int((cid == c).sum()) * K for c, (N, K) in enumerate(nk))
+
+    # plain: one launch per code over that code's frames
+    codes, outs, bufs, shapes = [], [], [], []
+    for c, (N, K) in enumerate(nk):
+        shape, src = tuned_or(N, K, masks[c], dtype,
+                              dict(threads=32, smem_stage_max=512, warp_stage_max=2048,
+                                   ctas_per_sm=0))
+        code = polar.polar_code_create(N, K, masks[c])
+        polar.polar_code_set_launch(code, dtype == "i8", stage_channel=2, **shape)
+        polar.polar_code_compile(code, dtype == "i8", llr[c].shape[0])
+        codes.append(code)
+        shapes.append(dict(shape, source=src))
+        bufs.append(torch.from_numpy(llr[c]).to(dev))
+        outs.append(torch.empty((llr[c].shape[0], (K + 7) // 8), dtype=torch.uint8, device=dev))
+    dec = polar.polar_decode_i8 if dtype == "i8" else polar.polar_decode
+
+    def plain(_):
+        for c in range(len(nk)):
+            dec(codes[c], bufs[c], outs[c])
+
+    # batched: frames in arrival order in one buffer, descriptors longest first
+    order = np.lexsort((np.arange(n), -np.array([nk[c][0] for c in cid])))
+    sizes = np.array([nk[c][0] for c in cid], np.int64)
+    orow = np.array([(nk[c][1] + 7) // 8 for c in cid], np.int64)
+    lo = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    oo = np.concatenate([[0], np.cumsum(orow)[:-1]])
+    flat = np.empty(int(sizes.sum()), llr[0].dtype)
+    pos = [0] * len(nk)
+    for i in range(n):  # arrival layout
+        c = cid[i]
+        flat[lo[i]: lo[i] + sizes[i]] = llr[c][pos[c]]
+        pos[c] += 1
+    d_flat = torch.from_numpy(flat).to(dev)
+    d_ids = torch.from_numpy(cid[order].astype(np.int32)).to(dev)
+    d_lo = torch.from_numpy(lo[order].astype(np.int64)).to(dev)
+    d_oo = torch.from_numpy(oo[order].astype(np.int64)).to(dev)
+    d_out = torch.zeros(int(orow.sum()), dtype=torch.uint8, device=dev)
+    bshape, bsrc = batch_shape(dtype)
+    t_c = time.perf_counter()
+    batch = polar.polar_batch_create(codes, dtype == "i8", bshape["threads"],
+                                     bshape["smem_stage_max"], bshape["warp_stage_max"])
+    t_c = time.perf_counter() - t_c
+    binfo = polar.polar_batch_info(batch)
+    s2 = torch.cuda.Stream(dev)
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        polar.polar_batch_decode(batch, d_ids, d_lo, d_oo, d_flat, d_out, stream=s2)
+    stream.wait_stream(s2)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        polar.polar_batch_decode(batch, d_ids, d_lo, d_oo, d_flat, d_out)
+    torch.cuda.synchronize()
+
+    # the two forms must agree bit for bit (both are the product path), and match
+    # the transmitted bits except for frame errors
+    plain(0)
+    graph.replay()
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy()
+    pos = [0] * len(nk)
+    agree, ferr = True, 0
+    for i in range(n):
+        c = cid[i]
+        a = got[oo[i]: oo[i] + orow[i]]
+        b = outs[c][pos[c]].cpu().numpy() if i < 64 else None
+        if b is not None and not np.array_equal(a, b):
+            agree = False
+        ferr += int(not np.array_equal(a, bits[c][pos[c]]))
+        pos[c] += 1
+    host_plain = [o.cpu().numpy() for o in outs]
+    pos = [0] * len(nk)
+    for i in range(n):
+        c = cid[i]
+        agree &= bool(np.array_equal(got[oo[i]: oo[i] + orow[i]], host_plain[c][pos[c]]))
+        pos[c] += 1
+
+    with ClockSampler(0) as clk:
+        plain_ms, _ = device_timed(torch, stream, plain, args.steps, args.warmup, 1)
+        batched_ms, _ = device_timed(torch, stream, lambda i: graph.replay(), args.steps,
+                                     args.warmup, 1)
+    per_code_ms = []
+    for c in range(len(nk)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            dec(codes[c], bufs[c], outs[c])
+        b.record(stream)
+        torch.cuda.synchronize()
+        per_code_ms.append(a.elapsed_time(b) / 3)
+    line = {
+        "metric": "info-bit Gbps, mixed-length batch", "mode": "mixed",
+        "value": info_bits * args.steps / (batched_ms * 1e-3) / 1e9, "unit": "Gbps",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": batched_ms / args.steps, "higher_is_better": True, "dtype": dtype,
+        "data": "synthetic",
+        "config": {"workload": f"mixed{n}", "codes": nk, "design_db": synth.MIXED_DESIGN_DB,
+                   "frames": n, "frames_per_code": [int((cid == c).sum()) for c in range(len(nk))],
+                   "llr": dtype, "l2": f"inputs {flat.nbytes / 2**20:.0f} MiB, larger than L2"},
+        "batched": {"gbps": info_bits * args.steps / (batched_ms * 1e-3) / 1e9,
+                    "step_ms": batched_ms / args.steps, "launches_per_step": 1,
+                    "cuda_graph": True, "shape": dict(bshape, source=bsrc), "launch": binfo,
+                    "compile_s": t_c},
+        "plain": {"gbps": info_bits * args.steps / (plain_ms * 1e-3) / 1e9,
+                  "step_ms": plain_ms / args.steps, "launches_per_step": len(nk),
+                  "per_code_ms": per_code_ms, "shapes": shapes},
+        "batched_over_plain": plain_ms / batched_ms,
+        "bits_agree": agree, "frame_errors": ferr, "input_gen_s": t_gen,
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- serving
+
+def serve_pool(P, seed):
+    """P frames of codes drawn uniformly from the mixed set, Eb/N0 uniform in
+    [2.0, 4.5] dB per frame, float32 LLRs, in one pinned buffer in arrival order."""
+    import torch
+
+    from paper_1504_00353_gb300 import polar
+    nk = synth.MIXED_CODES
+    masks, cid, llr, bits = mixed_inputs(P, "f32", seed, ebn0_range=(2.0, 4.5))
+    sizes = np.array([nk[c][0] for c in cid], np.int64)
+    orow = np.array([(nk[c][1] + 7) // 8 for c in cid], np.int64)
+    lo = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    oo = np.concatenate([[0], np.cumsum(orow)[:-1]])
+    host_llr = torch.empty(int(sizes.sum()), dtype=torch.float32).pin_memory()
+    hv = host_llr.numpy()
+    pos = [0] * len(nk)
+    want = []
+    for i in range(P):
+        c = cid[i]
+        hv[lo[i]: lo[i] + sizes[i]] = llr[c][pos[c]]
+        want.append(bits[c][pos[c]])
+        pos[c] += 1
+    reqs = np.zeros(P, polar.REQUEST_DTYPE)
+    reqs["code_id"], reqs["llr_off"], reqs["out_off"] = cid, lo * 4, oo
+    host_out = torch.zeros(int(orow.sum()), dtype=torch.uint8).pin_memory()
+    return masks, cid, reqs, host_llr, host_out, want, oo, orow
+
+
+def serve_run(polar, batch, reqs, host_llr, host_out, rate_fps, n_total, flags, slots,
+              budget, max_frames, seed):
+    """Poisson arrivals at rate_fps frames/s; requests i use pool entry i % P.
+    Returns per-request latencies (ns) and the wall time from the first arrival
+    to the last completion."""
+    P = reqs.size
+    done = np.zeros(P, np.uint64)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1e9 / rate_fps, n_total)
+    srv = polar.polar_server_create(batch, reqs, host_llr, host_out, done, budget, max_frames,
+                                    slots, flags)
+    t0 = time.monotonic_ns() + 2_000_000
+    arr = (t0 + np.cumsum(gaps)).astype(np.int64)
+    lat = np.zeros(n_total, np.int64)
+    published = harvested = 0
+    while harvested < n_total:
+        completed, adm, launches = polar.polar_server_progress(srv)
+        if completed > harvested:
+            idx = np.arange(harvested, completed)
+            lat[harvested:completed] = done[idx % P].astype(np.int64) - arr[harvested:completed]
+            harvested = completed
+        if published < n_total:
+            due = int(np.searchsorted(arr, time.monotonic_ns(), side="right"))
+            hi = min(due, completed + P, n_total)
+            if hi > published:
+                polar.polar_server_publish(srv, hi)
+                published = hi
+    t_end = int(done[(n_total - 1) % P])
+    polar.polar_server_destroy(srv)
+    return lat, (t_end - arr[0]) * 1e-9, adm, launches
+
+
+def run_serve(args):
+    """Serving loop at offered loads of coded Gbps: Poisson arrivals of frames of
+    the mixed code set (float32 LLRs, Eb/N0 uniform in [2, 4.5] dB), continuous
+    batching (overlapping launches, admission by device-memory budget) against
+    a plain queue decoding one launch per code, one batch at a time."""
+    import torch
+
+    from paper_1504_00353_gb300 import polar
+    torch.cuda.set_device(0)
+    nk = synth.MIXED_CODES
+    P = 16384
+    masks, cid, reqs, host_llr, host_out, want, oo, orow = serve_pool(P, seed=4)
+    mean_coded = float(np.mean([N for N, K in nk]))
+    mean_info = float(np.mean([K for N, K in nk]))
+    codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
+    bshape, bsrc = batch_shape("f32")
+    batch = polar.polar_batch_create(codes, False, bshape["threads"], bshape["smem_stage_max"],
+                                     bshape["warp_stage_max"])
+    budget = 4 << 30
+    arms = {"served": dict(flags=0, slots=4, max_frames=4096),
+            "plain": dict(flags=polar.SERVE_LAUNCH_PER_CODE, slots=1, max_frames=4096)}
+    # correctness gate: one pass over the pool through each arm, bits vs transmitted
+    gate = {}
+    for name, a in arms.items():
+        host_out.zero_()
+        serve_run(polar, batch, reqs, host_llr, host_out, 2e6, P, a["flags"], a["slots"], budget,
+                  a["max_frames"], seed=1)
+        ho = host_out.numpy()
+        gate[name] = ho.copy()
+    agree = bool(np.array_equal(gate["served"], gate["plain"]))
+    ferr = sum(int(not np.array_equal(gate["served"][oo[i]: oo[i] + orow[i]], want[i]))
+               for i in range(P))
+    results = []
+    with ClockSampler(0) as clk:
+        for load in [float(x) for x in args.loads.split(",")]:
+            rate = load * 1e9 / mean_coded
+            n_total = int(min(args.serve_max_frames, max(1000, rate * args.serve_seconds)))
+            row = {"offered_coded_gbps": load, "frames": n_total}
+            for name, a in arms.items():
+                lat, wall, adm, launches = serve_run(polar, batch, reqs, host_llr, host_out, rate,
+                                                     n_total, a["flags"], a["slots"], budget,
+                                                     a["max_frames"], seed=int(load * 7) + 11)
+                us = lat * 1e-3
+                row[name] = {"p50_us": float(np.percentile(us, 50)),
+                             "p99_us": float(np.percentile(us, 99)),
+                             "p999_us": float(np.percentile(us, 99.9)),
+                             "info_gbps": n_total * mean_info / wall / 1e9,
+                             "coded_gbps": n_total * mean_coded / wall / 1e9,
+                             "admissions": adm, "launches": launches,
+                             "frames_per_admission": n_total / max(adm, 1)}
+            results.append(row)
+            print(json.dumps({"load": row}), file=sys.stderr, flush=True)
+    top = max(results, key=lambda r: r["offered_coded_gbps"])
+    line = {
+        "metric": "served info-bit Gbps and p50/p99 frame latency (us)", "mode": "serve",
+        "value": top["served"]["info_gbps"], "unit": "Gbps", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve_mixed", "codes": nk, "design_db": synth.MIXED_DESIGN_DB,
+                   "ebn0_db": [2.0, 4.5], "arrivals": "Poisson", "pool_frames": P,
+                   "device_budget_bytes": budget, "arms": arms, "batch_shape": dict(bshape, source=bsrc),
+                   "latency": "completion seen by the serving thread minus scheduled arrival"},
+        "loads": results, "bits_agree": agree, "frame_errors_in_pool": ferr,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "mixed":
+        return run_mixed(args)
+    if args.mode == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         # the CPU oracle arm: rank 0 alone runs and prints, other ranks exit
         if int(os.environ.get("RANK", "0")) == 0:

@@ -234,11 +234,22 @@ typedef struct polar_batch polar_batch_t;
  *   smem_stage_max  per code, the largest alpha stage kept in shared memory
  *                   (power of two; NULL or 0 entries = 512 for 32 threads,
  *                   2048 otherwise). Larger stages use device scratch.
+ *   warp_stage_max  per code, the largest node handled by warp 0 alone: the
+ *                   tree depth at which work switches from CTA-wide to
+ *                   warp-level (power of two; NULL or 0 entries = 2048;
+ *                   raised to 256, the register-resident subtree size).
+ *   ctas_per_sm     cap on resident CTAs (frames) per SM, which also sets the
+ *                   register budget of the kernel (0 = as many as shared
+ *                   memory allows, at most 32).
+ * Returns POLAR_EINVAL for bad arguments or codes not created with this
+ * device current, POLAR_ECUDA if NVRTC is missing or compilation fails (log:
+ * polar_batch_log(NULL)), POLAR_ENOMEM if an allocation fails.
  * The descriptor table, the work counter and the scratch of every resident
  * CTA are allocated here, so polar_batch_decode allocates nothing and can be
  * captured in a CUDA graph. Blocking (NVRTC compile). */
 polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
                                 uint32_t threads, const uint32_t *smem_stage_max,
+                                const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
                                 polar_batch_t **out);
 
 void polar_batch_destroy(polar_batch_t *batch);
@@ -250,8 +261,10 @@ void polar_batch_destroy(polar_batch_t *batch);
  *               frame start: a multiple of 4 for float32, 16 for int8);
  *   out_off[i]  byte offset of frame i's ceil(K/8) output bytes in bits_out.
  * Frames are claimed in index order, so listing the longest codes first gives
- * the best balance. Calls on one batch decoder share its work counter and
- * scratch: they must not overlap on the GPU (issue them on one stream). */
+ * the best balance. The grid is min(resident CTAs, n_frames). Calls on one
+ * batch decoder share its work counter and scratch: they must not overlap on
+ * the GPU (issue them on one stream; the serving loop below has its own
+ * workspace per launch). */
 polar_status polar_batch_decode(polar_batch_t *batch, const uint32_t *code_id,
                                 const uint64_t *llr_off, const uint64_t *out_off,
                                 const void *llr, uint8_t *bits_out, size_t n_frames,
@@ -264,6 +277,78 @@ polar_status polar_batch_info(const polar_batch_t *batch, uint32_t *threads, uin
 /* NVRTC log of the batch decoder's compilation (never NULL). With batch =
  * NULL: the log of the last polar_batch_create that failed on this thread. */
 const char *polar_batch_log(const polar_batch_t *batch);
+
+/* ---- Serving loop: continuous batching onto a batch decoder ---- */
+
+typedef struct polar_server polar_server_t;
+
+/* One decode request: frame of code `code_id` (index into the batch decoder's
+ * codes) whose N channel LLRs (float32 or int8, the batch decoder's type) are
+ * at byte offset llr_off of the host input buffer and whose ceil(K/8) output
+ * bytes (information bits packed LSB first, as polar_decode) go to byte
+ * offset out_off of the host output buffer. Requests that follow one another
+ * and whose data are adjacent in the host buffers move in one copy. */
+typedef struct polar_request {
+    uint32_t code_id;
+    uint32_t reserved;
+    uint64_t llr_off;
+    uint64_t out_off;
+} polar_request;
+
+/* Start a serving loop on the current device (the batch decoder's). There is
+ * no counterpart in the paper, which decodes one frame or one batch per call;
+ * this is the serving form of the same decoder.
+ *   reqs, capacity   circular request array owned by the caller: request i
+ *                    is reqs[i % capacity]; it is read after polar_server_
+ *                    publish covers i and may be overwritten once request
+ *                    i is complete.
+ *   host_llr, host_out  caller-owned host buffers (pinned memory, e.g. from
+ *                    cudaMallocHost, for asynchronous copies) with their
+ *                    sizes in bytes; they must outlive the server.
+ *   done_ns          caller-owned array of `capacity` entries: the loop
+ *                    writes done_ns[i % capacity] = completion time of
+ *                    request i (CLOCK_MONOTONIC nanoseconds) before
+ *                    counting it complete.
+ *   device_budget_bytes  device memory for requests in flight (LLR ring and
+ *                    output ring; at least one frame of the longest code):
+ *                    a request is admitted when it fits.
+ *   max_frames       frames per launch (at most).
+ *   slots            launches in flight at once (1..64), each with its own
+ *                    stream, work counter and alpha scratch; device memory
+ *                    beyond the budget: slots x (scratch for max_frames
+ *                    frames + 20 bytes per frame).
+ *   flags            0, or POLAR_SERVE_LAUNCH_PER_CODE: each admission is
+ *                    decoded by one launch per code present (one after
+ *                    another on the slot's stream) instead of one launch for
+ *                    all; with slots = 1 this is a plain queue feeding
+ *                    one-launch-per-code batches, the baseline the mixed,
+ *                    overlapped form is measured against.
+ * A host thread admits published requests as slots and ring space free up,
+ * one launch of the batch decoder per admission (longest codes first), and
+ * retires finished launches in admission order. */
+#define POLAR_SERVE_LAUNCH_PER_CODE 1u
+polar_status polar_server_create(polar_batch_t *batch, const polar_request *reqs, size_t capacity,
+                                 const void *host_llr, size_t host_llr_bytes, uint8_t *host_out,
+                                 size_t host_out_bytes, uint64_t *done_ns,
+                                 size_t device_budget_bytes, uint32_t max_frames, uint32_t slots,
+                                 uint32_t flags, polar_server_t **out);
+
+/* Requests [0, n_published) have arrived (n_published never decreases).
+ * POLAR_EINVAL if a new request names an unknown code or lies outside the
+ * host buffers, or if n_published would overrun requests not yet complete
+ * (more than `capacity` outstanding); nothing is published then. */
+polar_status polar_server_publish(polar_server_t *server, uint64_t n_published);
+
+/* Requests completed (all of [0, *n_completed) are), admissions and kernel
+ * launches issued so far (NULL pointers are skipped). Returns the loop's
+ * sticky error: POLAR_ECUDA after a failed CUDA call (the loop then admits
+ * nothing more). */
+polar_status polar_server_progress(const polar_server_t *server, uint64_t *n_completed,
+                                   uint64_t *n_admissions, uint64_t *n_launches);
+
+/* Finish every published request (unless the loop failed), stop the loop and
+ * free the server. Returns the loop's error status. */
+polar_status polar_server_destroy(polar_server_t *server);
 
 /* Wait for `stream`, then read and clear the handle's device status word on
  * the current device. POLAR_ETIMEOUT if a bounded device wait expired since

@@ -1,0 +1,276 @@
+"""Launch-shape autotuner for the specialised decoders.
+
+For one code and LLR type it times candidate launch shapes on the GPU and keeps
+the fastest: threads per CTA (threads per frame), the largest alpha stage held
+in shared memory, the node size up to which warp 0 works alone (the tree depth
+where work switches from CTA-wide to warp-level), and the cap on resident CTAs
+(frames) per SM, which also sets the kernel's register budget. The search is
+coordinate-wise (threads, then stage cap, then warp threshold, then CTAs per
+SM); candidates of one round are compiled in parallel host threads (NVRTC) and
+timed one after another with CUDA events on a batch that fills the GPU.
+
+For a mixed batch the kernel has one block size for every code: the tuner picks
+the block size that minimises the mix's expected time per frame, then the
+per-code stage cap and warp threshold at that block size.
+
+Results are kept in a JSON table (``tuned_shapes.json`` beside this file) keyed
+by device name, code (N, K, hash of the frozen mask) and LLR type; ``lookup``
+returns an entry for a code, falling back to any entry with the same N, K and
+LLR type.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import statistics
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import polar
+
+TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_shapes.json")
+THREADS = (32, 64, 128, 256)
+STAGES = (256, 512, 1024, 2048, 4096)
+WARPS = (256, 512, 1024, 2048, 4096)
+_lock = threading.Lock()
+
+
+def mask_hash(mask) -> str:
+    return hashlib.sha1(np.ascontiguousarray(np.asarray(mask, np.uint8)).tobytes()).hexdigest()[:12]
+
+
+def code_key(N: int, K: int, mask, dtype: str) -> str:
+    return f"{N}_{K}_{mask_hash(mask)}_{dtype}"
+
+
+def device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def load_table(path: str = TABLE) -> dict:
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def save_table(table: dict, path: str = TABLE):
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(table, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    os.replace(tmp, path)
+
+
+def lookup(N: int, K: int, mask, dtype: str, table: dict | None = None, device: str | None = None):
+    """Tuned shape for a code, or None. Exact mask first, then same (N, K, dtype)."""
+    table = load_table() if table is None else table
+    dev = table.get(device or device_name(), {})
+    hit = dev.get(code_key(N, K, mask, dtype))
+    if hit:
+        return hit
+    for k, v in sorted(dev.items()):
+        parts = k.split("_")
+        if len(parts) == 4 and parts[0] == str(N) and parts[1] == str(K) and parts[3] == dtype:
+            return v
+    return None
+
+
+def synthetic_llr(N: int, n_frames: int, dtype: str, ebn0_db: float, rate: float, seed: int = 0):
+    """BPSK-AWGN LLRs of the all-zero codeword (a codeword of every polar code),
+    generated on the device: the decoder's work does not depend on the values."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    s2 = 1.0 / (2.0 * rate * 10.0 ** (ebn0_db / 10.0))
+    y = 1.0 + s2 ** 0.5 * torch.randn((n_frames, N), generator=g, device="cuda")
+    llr = (2.0 / s2) * y
+    if dtype == "i8":
+        return torch.clamp(torch.round(8.0 * llr), -127, 127).to(torch.int8)
+    return llr.float().contiguous()
+
+
+def frames_for(N: int, sms: int) -> int:
+    """Batch that keeps every SM busy with several waves of small CTAs."""
+    return int(max(sms * 48, min(1 << 17, (1 << 26) // N)))
+
+
+def _shape_key(s: dict) -> tuple:
+    return (s["threads"], s["smem_stage_max"], s["warp_stage_max"], s.get("ctas_per_sm", 0))
+
+
+def _compile(N, K, mask, dtype, shape, n_frames):
+    code = polar.polar_code_create(N, K, mask)
+    polar.polar_code_set_launch(code, dtype == "i8", threads=shape["threads"],
+                                smem_stage_max=shape["smem_stage_max"],
+                                warp_stage_max=shape["warp_stage_max"],
+                                ctas_per_sm=shape.get("ctas_per_sm", 0), stage_channel=2)
+    try:
+        polar.polar_code_compile(code, dtype == "i8", n_frames)
+    except polar.PolarError:
+        return None
+    return code
+
+
+def _time(code, dtype, llr, out, reps=3) -> float:
+    import torch
+    dec = polar.polar_decode_i8 if dtype == "i8" else polar.polar_decode
+    dec(code, llr, out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dec(code, llr, out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    return statistics.median(ts)
+
+
+class CodeTuner:
+    """Times launch shapes of one code; remembers every shape it measured."""
+
+    def __init__(self, N, K, mask, dtype, ebn0_db=3.0, n_frames=None, workers=8, log=None):
+        import torch
+        self.N, self.K, self.mask, self.dtype = N, K, np.asarray(mask, np.uint8), dtype
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        self.n_frames = n_frames or frames_for(N, sms)
+        self.llr = synthetic_llr(N, self.n_frames, dtype, ebn0_db, K / N)
+        self.out = torch.empty((self.n_frames, (K + 7) // 8), dtype=torch.uint8, device="cuda")
+        self.workers = workers
+        self.seen: dict[tuple, float] = {}  # shape key -> seconds per frame
+        self.log = log
+
+    def clamp(self, s) -> dict:
+        """The shape the library would use: stage cap at most N/2, warp threshold
+        at most N (larger values change nothing)."""
+        return dict(s, smem_stage_max=min(s["smem_stage_max"], max(self.N // 2, 64)),
+                    warp_stage_max=min(s["warp_stage_max"], max(self.N, 256)))
+
+    def measure(self, shapes) -> None:
+        todo = []
+        for s in map(self.clamp, shapes):
+            if _shape_key(s) not in self.seen and all(_shape_key(s) != _shape_key(x) for x in todo):
+                todo.append(s)
+        if not todo:
+            return
+        with ThreadPoolExecutor(max_workers=self.workers) as ex:
+            codes = list(ex.map(lambda s: _compile(self.N, self.K, self.mask, self.dtype, s,
+                                                   self.n_frames), todo))
+        for s, code in zip(todo, codes):
+            if code is None:
+                self.seen[_shape_key(s)] = float("inf")
+                continue
+            launch = polar.polar_code_get_launch(code, self.dtype == "i8", self.n_frames)
+            t = _time(code, self.dtype, self.llr, self.out) / self.n_frames if launch["unrolled"] \
+                else float("inf")
+            self.seen[_shape_key(s)] = t
+            if self.log:
+                self.log(f"  ({self.N},{self.K}) {self.dtype} {_shape_key(s)}: "
+                         f"{self.K / t / 1e9 if t < float('inf') else 0:.1f} Gbps")
+            del code
+
+    def best(self, threads=None) -> tuple[dict, float]:
+        cands = [(t, k) for k, t in self.seen.items() if threads is None or k[0] == threads]
+        t, k = min(cands)
+        return dict(threads=k[0], smem_stage_max=k[1], warp_stage_max=k[2], ctas_per_sm=k[3]), t
+
+    def tune(self, threads_options=THREADS, fixed_threads=None, tune_ctas=True) -> tuple[dict, float]:
+        def default(t):
+            return dict(threads=t, smem_stage_max=512 if t == 32 else 2048, warp_stage_max=2048,
+                        ctas_per_sm=0)
+        if fixed_threads is None:
+            self.measure([default(t) for t in threads_options])
+            cur, _ = self.best()
+        else:
+            self.measure([default(fixed_threads)])
+            cur, _ = self.best(fixed_threads)
+        T = cur["threads"]
+        self.measure([dict(cur, smem_stage_max=s) for s in STAGES])
+        cur, _ = self.best(T)
+        if T > 32:
+            self.measure([dict(cur, warp_stage_max=w) for w in WARPS])
+            cur, _ = self.best(T)
+        if tune_ctas:  # fewer resident frames per SM, more registers per thread
+            top = min(32, 2048 // T)
+            self.measure([dict(cur, ctas_per_sm=c) for c in (8, 12, 16, 20, 24, 28) if c < top])
+        return self.best(T)
+
+
+def tune_code(N, K, mask, dtype, table=None, save=True, tuner=None, **kw) -> dict:
+    """Tune one code; store and return its entry."""
+    tuner = tuner or CodeTuner(N, K, mask, dtype, **kw)
+    shape, t = tuner.tune()
+    entry = dict(shape, gbps=K / t / 1e9, n_frames=tuner.n_frames)
+    with _lock:
+        tab = load_table() if table is None else table
+        tab.setdefault(device_name(), {})[code_key(N, K, mask, dtype)] = entry
+        if save:
+            save_table(tab)
+    return entry
+
+
+def tune_batch(tuners, weights=None) -> dict:
+    """Shape of a mixed-batch decoder over the tuners' codes: one block size for
+    all codes (least expected time per frame of the mix, each code at its default
+    stage cap and warp threshold), then per-code stage cap and warp threshold
+    tuned at that block size. Returns dict(threads, smem_stage_max[],
+    warp_stage_max[], per_code_gbps[], expected_s_per_frame{threads: s})."""
+    w = np.ones(len(tuners)) / len(tuners) if weights is None else np.asarray(weights, float)
+    for tu in tuners:
+        tu.measure([dict(threads=t, smem_stage_max=512 if t == 32 else 2048, warp_stage_max=2048,
+                         ctas_per_sm=0) for t in THREADS])
+    cost = {t: float(sum(wi * tu.best(t)[1] for wi, tu in zip(w, tuners))) for t in THREADS}
+    T = min(cost, key=cost.get)
+    shapes = [tu.tune(fixed_threads=T, tune_ctas=False)[0] for tu in tuners]
+    return dict(threads=T, smem_stage_max=[s["smem_stage_max"] for s in shapes],
+                warp_stage_max=[s["warp_stage_max"] for s in shapes],
+                per_code_gbps=[tu.K / tu.best(T)[1] / 1e9 for tu in tuners],
+                expected_s_per_frame={str(t): c for t, c in cost.items()})
+
+
+def main(argv=None):
+    import argparse
+
+    import torch
+
+    from . import synth
+    p = argparse.ArgumentParser(description="tune launch shapes on the current GPU")
+    p.add_argument("--workload", action="append", default=[],
+                   help="a named workload of synth.WORKLOADS (repeatable)")
+    p.add_argument("--mixed", action="store_true", help="the mixed-length code set")
+    p.add_argument("--dtype", action="append", default=[], choices=["f32", "i8"])
+    p.add_argument("--out", default=TABLE)
+    a = p.parse_args(argv)
+    torch.cuda.set_device(0)
+    table = load_table(a.out)
+    # (N, K, mask, design dB, frames: the workload's batch, else enough to fill the GPU)
+    codes = [(w["N"], w["K"], synth.frozen_mask(w["N"], w["K"], w["design_db"]), w["design_db"],
+              w["n_frames"]) for w in (synth.WORKLOADS[n] for n in a.workload)]
+    if a.mixed:
+        codes += [(N, K, synth.frozen_mask(N, K, synth.MIXED_DESIGN_DB), synth.MIXED_DESIGN_DB,
+                   None) for N, K in synth.MIXED_CODES]
+    for dtype in a.dtype or ["i8"]:
+        tuners = []
+        for N, K, mask, db, nf in codes:
+            tu = CodeTuner(N, K, mask, dtype, ebn0_db=db, n_frames=nf, log=print)
+            e = tune_code(N, K, mask, dtype, table=table, save=False, tuner=tu)
+            print(f"({N},{K}) {dtype}: {e}", flush=True)
+            save_table(table, a.out)
+            tuners.append((db, tu))
+        if a.mixed:
+            mixed = [tu for db, tu in tuners if db == synth.MIXED_DESIGN_DB and
+                     (tu.N, tu.K) in synth.MIXED_CODES][-len(synth.MIXED_CODES):]
+            b = tune_batch(mixed)
+            table.setdefault(device_name(), {})[f"mixed_{dtype}"] = b
+            print(f"mixed {dtype}: {b}", flush=True)
+            save_table(table, a.out)
+        del tuners
+
+
+if __name__ == "__main__":
+    main()

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpolar_gb300.so")
 SOURCES = [os.path.join(CSRC, "polar_host.cpp"), os.path.join(CSRC, "polar_codegen.cpp"),
-           os.path.join(CSRC, "polar_batch.cpp"), os.path.join(CSRC, "polar_kernels.cu")]
+           os.path.join(CSRC, "polar_batch.cpp"), os.path.join(CSRC, "polar_serve.cpp"),
+           os.path.join(CSRC, "polar_kernels.cu")]
 GEN = os.path.join(HERE, "_build")  # generated include: polar_ops.cuh as a C++ string
 HEADERS = [os.path.join(CSRC, "polar_internal.h"), os.path.join(CSRC, "polar_ops.cuh"),
            os.path.join(ROOT, "include", "polar_gb300.h")]
@@ -58,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
            "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + GEN, "-o", tmp, *SOURCES,
-           "-ldl"]
+           "-ldl", "-lpthread"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

@@ -17,33 +17,6 @@
 
 using namespace polar;
 
-struct polar_batch {
-    bool is_i8 = false;
-    int device = -1;
-    uint32_t threads = 32;
-    std::vector<polar_code *> codes;
-    std::vector<uint32_t> S, W, R;
-    CompiledKernel ck;
-    LaunchShape shape{};
-    CodeDesc *d_codes = nullptr;
-    unsigned int *d_counter = nullptr;
-    void *scratch = nullptr;
-    size_t gstride = 0;
-    uint32_t alpha_elems = 0, beta_words = 0;
-    std::string log;
-
-    ~polar_batch() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (device >= 0) cudaSetDevice(device);
-        cudaFree(d_codes);
-        cudaFree(d_counter);
-        cudaFree(scratch);
-        if (ck.lib) cudaLibraryUnload(ck.lib);
-        if (cur >= 0) cudaSetDevice(cur);
-    }
-};
-
 namespace {
 
 // Log of the last polar_batch_create that failed on this thread.
@@ -57,16 +30,58 @@ polar_status st_of(cudaError_t e) {
 
 }  // namespace
 
+polar_batch::~polar_batch() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (device >= 0) cudaSetDevice(device);
+    cudaFree(d_codes);
+    cudaFree(d_counter);
+    cudaFree(scratch);
+    if (ck.lib) cudaLibraryUnload(ck.lib);
+    if (cur >= 0) cudaSetDevice(cur);
+}
+
+namespace polar {
+
+cudaError_t batch_launch(polar_batch *b, const uint32_t *code_id, const uint64_t *llr_off,
+                         const uint64_t *out_off, const void *llr, uint8_t *out, size_t n_frames,
+                         unsigned int *counter, void *scratch, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return e;
+    BatchArgs a{};
+    a.codes = b->d_codes;
+    a.code_id = code_id;
+    a.llr_off = reinterpret_cast<const unsigned long long *>(llr_off);
+    a.out_off = reinterpret_cast<const unsigned long long *>(out_off);
+    a.llr = llr;
+    a.out = out;
+    a.counter = counter;
+    a.gscratch = scratch;
+    a.gstride = b->gstride;
+    a.n_frames = n_frames;
+    a.smem_alpha_elems = b->alpha_elems;
+    a.smem_beta_words = b->beta_words;
+    LaunchShape sh = b->shape;
+    sh.grid = static_cast<uint32_t>(std::min<size_t>(sh.grid, n_frames));
+    return launch_compiled(&b->ck, sh, &a, stream);
+}
+
+}  // namespace polar
+
 extern "C" {
 
 polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
                                 uint32_t threads, const uint32_t *smem_stage_max,
+                                const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
                                 polar_batch_t **out) {
     if (!codes || !out || n_codes == 0 || n_codes > 64) return POLAR_EINVAL;
     if (threads == 0) threads = 32;
     if (threads % 32 || threads > 1024) return POLAR_EINVAL;
-    for (uint32_t c = 0; c < n_codes; ++c)
+    for (uint32_t c = 0; c < n_codes; ++c) {
         if (!codes[c]) return POLAR_EINVAL;
+        if (smem_stage_max && smem_stage_max[c] && !is_pow2(smem_stage_max[c])) return POLAR_EINVAL;
+        if (warp_stage_max && warp_stage_max[c] && !is_pow2(warp_stage_max[c])) return POLAR_EINVAL;
+    }
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();
@@ -77,22 +92,20 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
     b->is_i8 = is_i8 != 0;
     b->device = device;
     b->threads = threads;
-    const uint32_t es = b->is_i8 ? 1 : 4;
+    const size_t es = b->elem_bytes();
+    constexpr uint32_t kReg = 256;  // register-resident subtree size of every body
     std::vector<CodeDesc> desc(n_codes);
     std::vector<const polar_code *> cc;
     for (uint32_t c = 0; c < n_codes; ++c) {
         polar_code *code = codes[c];
         uint32_t s = smem_stage_max && smem_stage_max[c] ? smem_stage_max[c]
                                                          : (threads == 32 ? 512u : 2048u);
-        if (!is_pow2(s)) {
-            delete b;
-            return POLAR_EINVAL;
-        }
         s = std::min<uint32_t>(std::max<uint32_t>(s, 64), std::max<uint32_t>(code->N / 2, 1));
+        const uint32_t w = warp_stage_max && warp_stage_max[c] ? warp_stage_max[c] : 2048u;
         b->codes.push_back(code);
         b->S.push_back(s);
-        b->W.push_back(std::max<uint32_t>(2048, 256));
-        b->R.push_back(256);
+        b->W.push_back(std::max(w, kReg));  // register subtrees run inside warp-0 runs
+        b->R.push_back(kReg);
         cc.push_back(code);
         b->alpha_elems = std::max(b->alpha_elems, 2 * s);
         b->beta_words = std::max(b->beta_words, code->NW);
@@ -128,9 +141,14 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
         delete b;
         return POLAR_EINVAL;
     }
-    const uint32_t min_blocks = static_cast<uint32_t>(std::max<size_t>(
-        1, std::min<size_t>({size_t(228 * 1024) / (smem + 1024), size_t(2048 / threads), size_t(32)})));
-    const std::string src = generate_batch_source(cc, b->is_i8, b->S, b->W, b->R, threads, min_blocks);
+    // resident CTAs per SM the shared memory allows; the register budget of the
+    // generated kernel is capped so that this many fit (or ctas_per_sm if lower)
+    size_t min_blocks = std::min<size_t>({size_t(228 * 1024) / (smem + 1024), size_t(2048 / threads),
+                                          size_t(32)});
+    if (ctas_per_sm) min_blocks = std::min<size_t>(min_blocks, ctas_per_sm);
+    min_blocks = std::max<size_t>(min_blocks, 1);
+    const std::string src = generate_batch_source(cc, b->is_i8, b->S, b->W, b->R, threads,
+                                                  static_cast<uint32_t>(min_blocks));
     cudaError_t e = compile_source(src, &b->ck, &b->log, "polar_batch");
     if (e != cudaSuccess) {
         const polar_status st = st_of(e);
@@ -138,7 +156,8 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
         delete b;
         return st;
     }
-    const int occ = compiled_max_ctas(&b->ck, threads, smem);
+    int occ = compiled_max_ctas(&b->ck, threads, smem);
+    if (ctas_per_sm) occ = std::min<int>(occ, static_cast<int>(ctas_per_sm));
     if (occ <= 0) {
         g_failed_log = b->log + "\nno CTA of this shape can be resident (smem " +
                        std::to_string(smem) + " bytes, " + std::to_string(threads) + " threads)";
@@ -155,7 +174,7 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
         e = cudaMemcpy(b->d_codes, desc.data(), sizeof(CodeDesc) * n_codes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned int));
     if (e == cudaSuccess && b->gstride)
-        e = cudaMalloc(&b->scratch, size_t(b->shape.grid) * b->gstride * es);
+        e = cudaMalloc(&b->scratch, b->scratch_bytes(b->shape.grid));
     if (e != cudaSuccess) {
         const polar_status st = st_of(e);
         delete b;
@@ -179,24 +198,8 @@ polar_status polar_batch_decode(polar_batch_t *b, const uint32_t *code_id, const
         cudaGetLastError();
         return POLAR_ECUDA;
     }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return st_of(e);
-    BatchArgs a{};
-    a.codes = b->d_codes;
-    a.code_id = code_id;
-    a.llr_off = reinterpret_cast<const unsigned long long *>(llr_off);
-    a.out_off = reinterpret_cast<const unsigned long long *>(out_off);
-    a.llr = llr;
-    a.out = bits_out;
-    a.counter = b->d_counter;
-    a.gscratch = b->scratch;
-    a.gstride = b->gstride;
-    a.n_frames = n_frames;
-    a.smem_alpha_elems = b->alpha_elems;
-    a.smem_beta_words = b->beta_words;
-    e = launch_compiled(&b->ck, b->shape, &a, s);
-    return st_of(e);
+    return st_of(batch_launch(b, code_id, llr_off, out_off, llr, bits_out, n_frames, b->d_counter,
+                              b->scratch, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 polar_status polar_batch_info(const polar_batch_t *b, uint32_t *threads, uint32_t *grid,
@@ -205,7 +208,7 @@ polar_status polar_batch_info(const polar_batch_t *b, uint32_t *threads, uint32_
     if (threads) *threads = b->shape.threads;
     if (grid) *grid = b->shape.grid;
     if (smem_bytes) *smem_bytes = b->shape.smem_bytes;
-    if (scratch_bytes) *scratch_bytes = size_t(b->shape.grid) * b->gstride * (b->is_i8 ? 1 : 4);
+    if (scratch_bytes) *scratch_bytes = b->scratch_bytes(b->shape.grid);
     return POLAR_OK;
 }
 

@@ -76,6 +76,7 @@ polar_status ensure_device(polar_code *c, int device, DeviceState **out) {
 
 struct DeviceProps {
     int sms = 0;
+    int max_blocks_per_sm = 32;
     size_t smem_optin = 0;
 };
 
@@ -90,6 +91,8 @@ DeviceProps device_props(int device) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) == cudaSuccess) p.sms = v;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) == cudaSuccess)
         p.smem_optin = static_cast<size_t>(v);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxBlocksPerMultiprocessor, device) == cudaSuccess && v > 0)
+        p.max_blocks_per_sm = v;
     cache[device] = p;
     return p;
 }
@@ -607,6 +610,7 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
     const size_t per_cta = sh.smem_bytes + 1024;
     gsh.ctas_per_sm = static_cast<uint32_t>(std::max<size_t>(
         1, std::min<size_t>({size_t(228 * 1024) / per_cta, size_t(2048 / sh.threads),
+                             size_t(dp.max_blocks_per_sm),
                              size_t(n_frames + dp.sms - 1) / std::max(dp.sms, 1)})));
     if (code->user[is_i8 ? 1 : 0].ctas_per_sm)
         gsh.ctas_per_sm = std::min(gsh.ctas_per_sm, code->user[is_i8 ? 1 : 0].ctas_per_sm);

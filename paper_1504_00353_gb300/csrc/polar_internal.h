@@ -232,6 +232,31 @@ struct polar_code {
     ~polar_code();
 };
 
+// The mixed-batch decoder behind polar_batch_t.
+struct polar_batch {
+    bool is_i8 = false;
+    int device = -1;
+    uint32_t threads = 32;
+    std::vector<polar_code *> codes;
+    std::vector<uint32_t> S, W, R;
+    polar::CompiledKernel ck;
+    polar::LaunchShape shape{};
+    polar::CodeDesc *d_codes = nullptr;
+    unsigned int *d_counter = nullptr;
+    void *scratch = nullptr;
+    size_t gstride = 0;  // scratch elements per CTA
+    uint32_t alpha_elems = 0, beta_words = 0;
+    std::string log;
+
+    size_t elem_bytes() const { return is_i8 ? 1 : 4; }
+    // Scratch bytes one launch over n_frames frames needs.
+    size_t scratch_bytes(size_t n_frames) const {
+        const size_t g = n_frames < shape.grid ? n_frames : shape.grid;
+        return g * gstride * elem_bytes();
+    }
+    ~polar_batch();
+};
+
 namespace polar {
 // Source text of the decoder specialised to `code` for one launch shape.
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
@@ -253,4 +278,11 @@ int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes);
 // Launch a compiled decoder on the current device.
 cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const void *args,
                             cudaStream_t stream);
+// Launch the batch decoder over n_frames frames with the given work counter and
+// alpha scratch (grid = min(resident CTAs, n_frames)); zeroes the counter on
+// the stream first. polar_batch_decode passes the batch's own workspace, the
+// serving loop one workspace per in-flight launch.
+cudaError_t batch_launch(polar_batch *b, const uint32_t *code_id, const uint64_t *llr_off,
+                         const uint64_t *out_off, const void *llr, uint8_t *out, size_t n_frames,
+                         unsigned int *counter, void *scratch, cudaStream_t stream);
 }  // namespace polar

@@ -26,8 +26,13 @@ EXPORTS = [
     "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
     "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_log",
     "polar_decode_noalloc", "polar_batch_create", "polar_batch_destroy", "polar_batch_decode",
-    "polar_batch_info", "polar_batch_log",
+    "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
+    "polar_server_progress", "polar_server_destroy",
 ]
+
+# struct polar_request
+REQUEST_DTYPE = np.dtype([("code_id", "<u4"), ("reserved", "<u4"), ("llr_off", "<u8"),
+                          ("out_off", "<u8")])
 
 
 class PolarError(RuntimeError):
@@ -64,11 +69,19 @@ def _load():
         "polar_code_compile": ([vp, st, sz, u32], st),
         "polar_code_compile_log": ([vp], ctypes.c_char_p),
         "polar_code_check": ([vp, vp], st),
-        "polar_batch_create": ([ctypes.POINTER(vp), u32, st, u32, u32p, ctypes.POINTER(vp)], st),
+        "polar_batch_create": ([ctypes.POINTER(vp), u32, st, u32, u32p, u32p, u32,
+                                ctypes.POINTER(vp)], st),
         "polar_batch_destroy": ([vp], None),
         "polar_batch_decode": ([vp, vp, vp, vp, vp, vp, sz, vp], st),
         "polar_batch_info": ([vp, u32p, u32p, szp, szp], st),
         "polar_batch_log": ([vp], ctypes.c_char_p),
+        "polar_server_create": ([vp, vp, sz, vp, sz, vp, sz, vp, sz, u32, u32, u32,
+                                 ctypes.POINTER(vp)], st),
+        "polar_server_publish": ([vp, ctypes.c_uint64], st),
+        "polar_server_progress": ([vp, ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_uint64)], st),
+        "polar_server_destroy": ([vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -294,13 +307,19 @@ class PolarBatch:
             self.handle = ctypes.c_void_p(0)
 
 
-def polar_batch_create(codes, is_i8: bool, threads: int = 0, smem_stage_max=None) -> PolarBatch:
+def polar_batch_create(codes, is_i8: bool, threads: int = 0, smem_stage_max=None,
+                       warp_stage_max=None, ctas_per_sm: int = 0) -> PolarBatch:
+    """One persistent decoder for frames of any of `codes`; per-code shared-memory
+    stage cap and warp threshold (lists, 0 = default)."""
     arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
-    sm = None
-    if smem_stage_max is not None:
-        sm = (ctypes.c_uint32 * len(codes))(*[int(v) for v in smem_stage_max])
+
+    def per_code(v):
+        return None if v is None else (ctypes.c_uint32 * len(codes))(*[int(x) for x in v])
+
     h = ctypes.c_void_p()
-    st = _lib.polar_batch_create(arr, len(codes), int(bool(is_i8)), threads, sm, ctypes.byref(h))
+    st = _lib.polar_batch_create(arr, len(codes), int(bool(is_i8)), threads,
+                                 per_code(smem_stage_max), per_code(warp_stage_max), ctas_per_sm,
+                                 ctypes.byref(h))
     if st != 0:
         raise PolarError(st, "polar_batch_create: " +
                          (_lib.polar_batch_log(None) or b"").decode(errors="replace")[-3000:])
@@ -333,3 +352,74 @@ def polar_batch_info(batch: PolarBatch) -> dict:
 
 def polar_batch_log(batch: PolarBatch) -> str:
     return (_lib.polar_batch_log(batch.handle) or b"").decode(errors="replace")
+
+
+def _host_ptr(buf):
+    """Address and size in bytes of a host buffer (numpy array or CPU tensor)."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("host buffers must be contiguous")
+        return buf.ctypes.data, buf.nbytes
+    if buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("host buffers must be contiguous CPU tensors")
+    return buf.data_ptr(), buf.numel() * buf.element_size()
+
+
+class PolarServer:
+    """Owns a polar_server_t; keeps the batch decoder and the host buffers alive."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    def destroy(self) -> int:
+        h = getattr(self, "handle", None)
+        st = 0
+        if h is not None and h.value:
+            st = _lib.polar_server_destroy(h)
+            self.handle = ctypes.c_void_p(0)
+        return st
+
+    def __del__(self):
+        self.destroy()
+
+
+SERVE_LAUNCH_PER_CODE = 1
+
+
+def polar_server_create(batch: PolarBatch, reqs: np.ndarray, host_llr, host_out, done_ns: np.ndarray,
+                        device_budget_bytes: int, max_frames: int, slots: int,
+                        flags: int = 0) -> PolarServer:
+    """Serving loop over `batch`. reqs: REQUEST_DTYPE array (circular, capacity =
+    len); host_llr / host_out: host buffers (pinned CPU tensors for overlap);
+    done_ns: uint64 array of len(reqs) receiving completion times; flags:
+    SERVE_LAUNCH_PER_CODE for one launch per code in each admission."""
+    if reqs.dtype != REQUEST_DTYPE or not reqs.flags.c_contiguous:
+        raise TypeError("reqs must be a contiguous REQUEST_DTYPE array")
+    if done_ns.dtype != np.uint64 or done_ns.size != reqs.size or not done_ns.flags.c_contiguous:
+        raise TypeError("done_ns must be a contiguous uint64 array of len(reqs) entries")
+    lp, lb = _host_ptr(host_llr)
+    op, ob = _host_ptr(host_out)
+    h = ctypes.c_void_p()
+    _check(_lib.polar_server_create(batch.handle, ctypes.c_void_p(reqs.ctypes.data), reqs.size,
+                                    ctypes.c_void_p(lp), lb, ctypes.c_void_p(op), ob,
+                                    ctypes.c_void_p(done_ns.ctypes.data), device_budget_bytes,
+                                    max_frames, slots, flags, ctypes.byref(h)),
+           "polar_server_create")
+    return PolarServer(h.value, (batch, reqs, host_llr, host_out, done_ns))
+
+
+def polar_server_publish(server: PolarServer, n_published: int):
+    _check(_lib.polar_server_publish(server.handle, n_published), "polar_server_publish")
+
+
+def polar_server_progress(server: PolarServer):
+    """(completed, admissions, launches); raises on the loop's sticky error."""
+    c, a, n = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.polar_server_progress(server.handle, ctypes.byref(c), ctypes.byref(a),
+                                      ctypes.byref(n)), "polar_server_progress")
+    return c.value, a.value, n.value
+
+
+def polar_server_destroy(server: PolarServer):
+    _check(server.destroy(), "polar_server_destroy")

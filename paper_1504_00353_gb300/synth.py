@@ -111,6 +111,12 @@ def bits_from_packed_codewords(packed: np.ndarray, N: int) -> np.ndarray:
 
 
 # Workloads named by what they are (code, channel, size).
+# Mixed-length set: frames drawn uniformly from these codes, every frozen set
+# by the construction above at MIXED_DESIGN_DB, channel at the same Eb/N0.
+MIXED_CODES = [(256, 128), (1024, 512), (2048, 1723), (16384, 14746), (32768, 29492)]
+MIXED_DESIGN_DB = 3.0
+MIXED_FRAMES = 65536
+
 WORKLOADS = {
     "n1024_k512_2.5db": dict(N=1024, K=512, design_db=2.5, ebn0_db=2.5, seed=0,
                              n_frames=10000),

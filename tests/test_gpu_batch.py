@@ -89,3 +89,49 @@ def test_mixed_batch_in_cuda_graph():
         g.replay()
         torch.cuda.synchronize()
         check(masks2, cid2, llrs2, out.cpu().numpy(), oo2)
+
+
+def test_mixed_full_size_sampled():
+    """The full mixed workload in one launch: 65,536 frames drawn uniformly from
+    the five codes (int8, 3.0 dB). About 90 sampled frames (random positions plus
+    the first and last frame of every code) carry random codewords and must
+    equal the oracle's decode; the other frames carry noisy all-zero codewords
+    (a codeword of every code) so that the launch has its full size and mix."""
+    nk = synth.MIXED_CODES
+    n = synth.MIXED_FRAMES
+    rng = np.random.default_rng(2024)
+    masks = [synth.frozen_mask(N, K, synth.MIXED_DESIGN_DB) for N, K in nk]
+    cid = np.sort(rng.integers(0, len(nk), n))[::-1].copy()  # longest codes first
+    sizes = np.array([nk[c][0] for c in cid], np.int64)
+    orow = np.array([(nk[c][1] + 7) // 8 for c in cid], np.int64)
+    lo = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    oo = np.concatenate([[0], np.cumsum(orow)[:-1]])
+    flat = np.empty(int(sizes.sum()), np.int8)
+    sample = set(rng.choice(n, 80, replace=False).tolist()) | {0, n - 1}
+    for c in range(len(nk)):  # first and last frame of every code
+        idx = np.flatnonzero(cid == c)
+        sample |= {int(idx[0]), int(idx[-1])}
+    for c, (N, K) in enumerate(nk):  # noisy all-zero codewords, one code at a time
+        idx = np.flatnonzero(cid == c)
+        y = synth.awgn_llr(rng, np.zeros((idx.size, N), np.uint8), synth.MIXED_DESIGN_DB, K / N)
+        q = synth.quantize_i8(y)
+        for j, i in enumerate(idx):
+            flat[lo[i]: lo[i] + N] = q[j]
+    want = {}
+    for i in sorted(sample):  # sampled frames: random codewords from the oracle encoder
+        N, K = nk[cid[i]]
+        d = synth.info_bits(rng, 1, K)
+        x = oracle.encode_systematic(masks[cid[i]], d[0])[None]
+        q = synth.quantize_i8(synth.awgn_llr(rng, x, synth.MIXED_DESIGN_DB, K / N))[0]
+        flat[lo[i]: lo[i] + N] = q
+        want[i] = oracle.decode_batch(masks[cid[i]], q[None])[0]
+    codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
+    batch = polar.polar_batch_create(codes, True, 32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.full((int(orow.sum()),), 0xA5, dtype=torch.uint8, device="cuda")
+    polar.polar_batch_decode(batch, dev(cid.astype(np.int32)), dev(lo), dev(oo), dev(flat), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for i, w in want.items():
+        assert np.array_equal(got[oo[i]: oo[i] + orow[i]], w), i
+    assert (got != 0xA5).any()
