@@ -63,7 +63,9 @@ def parse():
     p.add_argument("--loads", default="1,10,50,200", help="serve: offered loads, coded Gbps")
     p.add_argument("--serve-seconds", type=float, default=1.0,
                    help="serve: seconds of arrivals per load (at most --serve-max-frames)")
-    p.add_argument("--serve-max-frames", type=int, default=1_000_000)
+    p.add_argument("--serve-max-frames", type=int, default=500_000)
+    p.add_argument("--serve-pool", choices=["host", "device"], default="host",
+                   help="serve: LLR pool in pinned host memory or in device memory")
     return p.parse_args()
 
 
@@ -118,8 +120,9 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=200):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
 
@@ -127,7 +130,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -573,8 +576,8 @@ def batch_shape(dtype):
         e = None
     if e:
         return dict(threads=e["threads"], smem_stage_max=e["smem_stage_max"],
-                    warp_stage_max=e["warp_stage_max"]), "tuned"
-    return dict(threads=32, smem_stage_max=None, warp_stage_max=None), "default"
+                    warp_stage_max=e["warp_stage_max"], ctas_per_sm=e.get("ctas_per_sm", 0)), "tuned"
+    return dict(threads=32, smem_stage_max=None, warp_stage_max=None, ctas_per_sm=0), "default"
 
 
 def run_mixed(args):
@@ -635,7 +638,8 @@ def run_mixed(args):
     bshape, bsrc = batch_shape(dtype)
     t_c = time.perf_counter()
     batch = polar.polar_batch_create(codes, dtype == "i8", bshape["threads"],
-                                     bshape["smem_stage_max"], bshape["warp_stage_max"])
+                                     bshape["smem_stage_max"], bshape["warp_stage_max"],
+                                     bshape["ctas_per_sm"])
     t_c = time.perf_counter() - t_c
     binfo = polar.polar_batch_info(batch)
     s2 = torch.cuda.Stream(dev)
@@ -786,39 +790,65 @@ def run_serve(args):
     codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
     bshape, bsrc = batch_shape("f32")
     batch = polar.polar_batch_create(codes, False, bshape["threads"], bshape["smem_stage_max"],
-                                     bshape["warp_stage_max"])
+                                     bshape["warp_stage_max"], bshape["ctas_per_sm"])
     budget = 4 << 30
     arms = {"served": dict(flags=0, slots=4, max_frames=4096),
             "plain": dict(flags=polar.SERVE_LAUNCH_PER_CODE, slots=1, max_frames=4096)}
+    if args.serve_pool == "device":  # LLR pool in HBM: isolates the scheduler from the host link
+        host_llr = host_llr.cuda()
+        host_out = host_out.cuda()
     # correctness gate: one pass over the pool through each arm, bits vs transmitted
     gate = {}
     for name, a in arms.items():
         host_out.zero_()
         serve_run(polar, batch, reqs, host_llr, host_out, 2e6, P, a["flags"], a["slots"], budget,
                   a["max_frames"], seed=1)
-        ho = host_out.numpy()
-        gate[name] = ho.copy()
+        gate[name] = host_out.cpu().numpy().copy()
     agree = bool(np.array_equal(gate["served"], gate["plain"]))
     ferr = sum(int(not np.array_equal(gate["served"][oo[i]: oo[i] + orow[i]], want[i]))
                for i in range(P))
+    # host-to-device copy bandwidth from pinned memory: float32 LLRs cross this
+    # link, so it bounds the coded rate the loop can take (4 bytes per coded bit)
+    big = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+    dbig = torch.empty(1 << 28, dtype=torch.float32, device="cuda")
+    dbig.copy_(big, non_blocking=True)
+    torch.cuda.synchronize()
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_.record()
+    for _ in range(3):
+        dbig.copy_(big, non_blocking=True)
+    b_.record()
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * big.numel() * 4 / (a_.elapsed_time(b_) * 1e-3) / 1e9
+    del big, dbig
     results = []
-    with ClockSampler(0) as clk:
+    reps = 2
+    # clocks sampled once a second here: the serving loop's latency tail is what
+    # is measured, and the sampler's device queries are kept rare
+    with ClockSampler(0, interval_ms=1000) as clk:
         for load in [float(x) for x in args.loads.split(",")]:
             rate = load * 1e9 / mean_coded
             n_total = int(min(args.serve_max_frames, max(1000, rate * args.serve_seconds)))
-            row = {"offered_coded_gbps": load, "frames": n_total}
-            for name, a in arms.items():
-                lat, wall, adm, launches = serve_run(polar, batch, reqs, host_llr, host_out, rate,
-                                                     n_total, a["flags"], a["slots"], budget,
-                                                     a["max_frames"], seed=int(load * 7) + 11)
-                us = lat * 1e-3
-                row[name] = {"p50_us": float(np.percentile(us, 50)),
-                             "p99_us": float(np.percentile(us, 99)),
-                             "p999_us": float(np.percentile(us, 99.9)),
-                             "info_gbps": n_total * mean_info / wall / 1e9,
-                             "coded_gbps": n_total * mean_coded / wall / 1e9,
-                             "admissions": adm, "launches": launches,
-                             "frames_per_admission": n_total / max(adm, 1)}
+            row = {"offered_coded_gbps": load, "frames": n_total, "reps": reps}
+            runs = {name: [] for name in arms}
+            for r in range(reps):  # arms interleaved, each run with its own arrivals
+                for name, a in arms.items():
+                    lat, wall, adm, launches = serve_run(polar, batch, reqs, host_llr, host_out,
+                                                         rate, n_total, a["flags"], a["slots"],
+                                                         budget, a["max_frames"],
+                                                         seed=int(load * 7) + 11 + 1000 * r)
+                    us = lat * 1e-3
+                    runs[name].append({"p50_us": float(np.percentile(us, 50)),
+                                       "p99_us": float(np.percentile(us, 99)),
+                                       "p999_us": float(np.percentile(us, 99.9)),
+                                       "info_gbps": n_total * mean_info / wall / 1e9,
+                                       "coded_gbps": n_total * mean_coded / wall / 1e9,
+                                       "admissions": adm, "launches": launches,
+                                       "frames_per_admission": n_total / max(adm, 1)})
+            for name, rs in runs.items():
+                # median over repetitions of each statistic, every repetition kept
+                row[name] = {k: float(np.median([x[k] for x in rs])) for k in rs[0]}
+                row[name]["runs"] = rs
             results.append(row)
             print(json.dumps({"load": row}), file=sys.stderr, flush=True)
     top = max(results, key=lambda r: r["offered_coded_gbps"])
@@ -826,10 +856,13 @@ def run_serve(args):
         "metric": "served info-bit Gbps and p50/p99 frame latency (us)", "mode": "serve",
         "value": top["served"]["info_gbps"], "unit": "Gbps", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serve_mixed", "codes": nk, "design_db": synth.MIXED_DESIGN_DB,
+        "config": {"workload": f"serve_mixed_{args.serve_pool}_pool", "codes": nk,
+                   "design_db": synth.MIXED_DESIGN_DB, "pool": args.serve_pool,
                    "ebn0_db": [2.0, 4.5], "arrivals": "Poisson", "pool_frames": P,
                    "device_budget_bytes": budget, "arms": arms, "batch_shape": dict(bshape, source=bsrc),
-                   "latency": "completion seen by the serving thread minus scheduled arrival"},
+                   "latency": "completion seen by the serving thread minus scheduled arrival",
+                   "h2d_pinned_gbs": h2d_gbs,
+                   "h2d_bound_coded_gbps": h2d_gbs * 8 / 32},
         "loads": results, "bits_agree": agree, "frame_errors_in_pool": ferr,
         "clocks": clk.summary(),
     }

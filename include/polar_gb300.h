@@ -302,9 +302,10 @@ typedef struct polar_request {
  *                    is reqs[i % capacity]; it is read after polar_server_
  *                    publish covers i and may be overwritten once request
  *                    i is complete.
- *   host_llr, host_out  caller-owned host buffers (pinned memory, e.g. from
- *                    cudaMallocHost, for asynchronous copies) with their
- *                    sizes in bytes; they must outlive the server.
+ *   host_llr, host_out  caller-owned buffers with their sizes in bytes, in
+ *                    pinned host memory (e.g. from cudaMallocHost; copies are
+ *                    asynchronous) or in device memory of this GPU (copies
+ *                    stay on the device); they must outlive the server.
  *   done_ns          caller-owned array of `capacity` entries: the loop
  *                    writes done_ns[i % capacity] = completion time of
  *                    request i (CLOCK_MONOTONIC nanoseconds) before

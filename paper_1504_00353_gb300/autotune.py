@@ -115,11 +115,23 @@ def _compile(N, K, mask, dtype, shape, n_frames):
     return code
 
 
-def _time(code, dtype, llr, out, reps=3) -> float:
+def _warm(fn, seconds=0.05):
+    """Run fn until `seconds` of wall time have passed (at least 3 times), so
+    that the GPU has left its idle clocks before a candidate is timed."""
+    import time
+
+    import torch
+    t0, k = time.perf_counter(), 0
+    while k < 3 or time.perf_counter() - t0 < seconds:
+        fn()
+        torch.cuda.synchronize()
+        k += 1
+
+
+def _time(code, dtype, llr, out, reps=5) -> float:
     import torch
     dec = polar.polar_decode_i8 if dtype == "i8" else polar.polar_decode
-    dec(code, llr, out)
-    torch.cuda.synchronize()
+    _warm(lambda: dec(code, llr, out))
     ts = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -214,12 +226,54 @@ def tune_code(N, K, mask, dtype, table=None, save=True, tuner=None, **kw) -> dic
     return entry
 
 
-def tune_batch(tuners, weights=None) -> dict:
-    """Shape of a mixed-batch decoder over the tuners' codes: one block size for
-    all codes (least expected time per frame of the mix, each code at its default
-    stage cap and warp threshold), then per-code stage cap and warp threshold
-    tuned at that block size. Returns dict(threads, smem_stage_max[],
-    warp_stage_max[], per_code_gbps[], expected_s_per_frame{threads: s})."""
+def mixed_sample(tuners, n_frames, seed=0):
+    """A device-resident mixed batch for timing: frames of the tuners' codes in
+    equal expected shares, stored code by code, descriptors longest code first
+    (the order a batch is claimed in). Returns (code_id, llr_off, out_off, llr,
+    out) tensors."""
+    import torch
+    rng = np.random.default_rng(seed)
+    counts = np.bincount(rng.integers(0, len(tuners), n_frames), minlength=len(tuners))
+    parts, ids, lo, oo = [], [], [], []
+    pos = opos = 0
+    for c in sorted(range(len(tuners)), key=lambda c: -tuners[c].N):
+        tu, m = tuners[c], int(counts[c])
+        idx = torch.arange(m, device="cuda") % tu.n_frames
+        parts.append(tu.llr[idx].reshape(-1))
+        ids += [c] * m
+        lo += [pos + j * tu.N for j in range(m)]
+        oo += [opos + j * ((tu.K + 7) // 8) for j in range(m)]
+        pos += m * tu.N
+        opos += m * ((tu.K + 7) // 8)
+    dev = lambda a, t: torch.tensor(a, dtype=t, device="cuda")
+    out = torch.empty(opos, dtype=torch.uint8, device="cuda")
+    return (dev(ids, torch.int32), dev(lo, torch.int64), dev(oo, torch.int64), torch.cat(parts), out)
+
+
+def time_batch(batch, sample, reps=5) -> float:
+    import torch
+    ids, lo, oo, llr, out = sample
+    _warm(lambda: polar.polar_batch_decode(batch, ids, lo, oo, llr, out))
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        polar.polar_batch_decode(batch, ids, lo, oo, llr, out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    return statistics.median(ts)
+
+
+def tune_batch(tuners, weights=None, sample_frames=16384, workers=6, log=None) -> dict:
+    """Shape of a mixed-batch decoder over the tuners' codes. (1) One block size
+    for all codes: least expected time per frame of the mix, each code at its
+    default stage cap and warp threshold in its own kernel. (2) Per-code stage
+    cap and warp threshold tuned at that block size. (3) The batch kernel
+    itself, timed on a mixed sample: one kernel's shared memory (the largest
+    code's) and register budget bound every code's resident frames, so caps on
+    the stage size and on resident CTAs per SM are tried jointly. Returns
+    dict(threads, smem_stage_max[], warp_stage_max[], ctas_per_sm, gbps, ...)."""
     w = np.ones(len(tuners)) / len(tuners) if weights is None else np.asarray(weights, float)
     for tu in tuners:
         tu.measure([dict(threads=t, smem_stage_max=512 if t == 32 else 2048, warp_stage_max=2048,
@@ -227,10 +281,43 @@ def tune_batch(tuners, weights=None) -> dict:
     cost = {t: float(sum(wi * tu.best(t)[1] for wi, tu in zip(w, tuners))) for t in THREADS}
     T = min(cost, key=cost.get)
     shapes = [tu.tune(fixed_threads=T, tune_ctas=False)[0] for tu in tuners]
-    return dict(threads=T, smem_stage_max=[s["smem_stage_max"] for s in shapes],
-                warp_stage_max=[s["warp_stage_max"] for s in shapes],
+    S0 = [s["smem_stage_max"] for s in shapes]
+    W0 = [s["warp_stage_max"] for s in shapes]
+    codes = [polar.polar_code_create(tu.N, tu.K, tu.mask) for tu in tuners]
+    cands = []
+    for cap in (None, 2048, 1024, 512, 256):
+        S = [min(x, cap) if cap else x for x in S0]
+        for cps in ((0, 28, 24) if T == 32 else (0,)):
+            c = (tuple(S), cps)
+            if c not in [x for x in cands]:
+                cands.append(c)
+
+    def build(c):
+        try:
+            return polar.polar_batch_create(codes, tuners[0].dtype == "i8", T, list(c[0]), W0, c[1])
+        except polar.PolarError:
+            return None
+
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        batches = list(ex.map(build, cands))
+    sample = mixed_sample(tuners, sample_frames)
+    ids = sample[0].cpu().numpy()
+    bits = float(sum(tuners[c].K for c in ids))
+    results = []
+    for c, b in zip(cands, batches):
+        if b is None:
+            continue
+        t = time_batch(b, sample)
+        results.append((t, c, polar.polar_batch_info(b)))
+        if log:
+            log(f"  batch T={T} S={list(c[0])} cps={c[1]}: {bits / t / 1e9:.1f} Gbps "
+                f"(grid {results[-1][2]['grid']})")
+        del b
+    t, (S, cps), info = min(results, key=lambda r: r[0])
+    return dict(threads=T, smem_stage_max=list(S), warp_stage_max=W0, ctas_per_sm=cps,
+                gbps=bits / t / 1e9, grid=info["grid"], sample_frames=sample_frames,
                 per_code_gbps=[tu.K / tu.best(T)[1] / 1e9 for tu in tuners],
-                expected_s_per_frame={str(t): c for t, c in cost.items()})
+                expected_s_per_frame={str(k): v for k, v in cost.items()})
 
 
 def main(argv=None):
@@ -265,7 +352,7 @@ def main(argv=None):
         if a.mixed:
             mixed = [tu for db, tu in tuners if db == synth.MIXED_DESIGN_DB and
                      (tu.N, tu.K) in synth.MIXED_CODES][-len(synth.MIXED_CODES):]
-            b = tune_batch(mixed)
+            b = tune_batch(mixed, log=print)
             table.setdefault(device_name(), {})[f"mixed_{dtype}"] = b
             print(f"mixed {dtype}: {b}", flush=True)
             save_table(table, a.out)

@@ -3,7 +3,8 @@
 //
 // Requests are descriptors in a caller-owned circular array; each names a
 // code and the place of its channel LLRs and of its output bytes in two
-// caller-owned host buffers (pinned memory for asynchronous copies). The
+// caller-owned buffers: pinned host memory (asynchronous copies over the
+// host link) or device memory (the copies stay in HBM). The
 // caller publishes requests by advancing a count. One host thread runs the
 // loop: whenever a launch slot is free and published requests wait, it admits
 // as many as fit in the device LLR and output rings (the memory budget) and in
@@ -205,7 +206,7 @@ struct polar_server {
             const polar_request &rl_last = reqs[(s.first + m - 1) % capacity];
             const size_t tail_pad = llr_bytes(rl_last.code_id) - size_t(code_N[rl_last.code_id]) * es;
             e = cudaMemcpyAsync(d_llr + dl[j] * es, h_llr + r0.llr_off, len - tail_pad,
-                                cudaMemcpyHostToDevice, s.stream);
+                                cudaMemcpyDefault, s.stream);
             j = m;
         }
         // one launch over the admitted frames, or (per-code policy) one launch
@@ -233,7 +234,7 @@ struct polar_server {
                 len += out_bytes(r.code_id);
                 ++m;
             }
-            e = cudaMemcpyAsync(h_out + r0.out_off, d_out + dout[j], len, cudaMemcpyDeviceToHost,
+            e = cudaMemcpyAsync(h_out + r0.out_off, d_out + dout[j], len, cudaMemcpyDefault,
                                 s.stream);
             j = m;
         }

@@ -354,14 +354,15 @@ def polar_batch_log(batch: PolarBatch) -> str:
     return (_lib.polar_batch_log(batch.handle) or b"").decode(errors="replace")
 
 
-def _host_ptr(buf):
-    """Address and size in bytes of a host buffer (numpy array or CPU tensor)."""
+def _buf_ptr(buf):
+    """Address and size in bytes of a request buffer: a numpy array, a CPU tensor
+    (pinned for asynchronous copies) or a CUDA tensor."""
     if isinstance(buf, np.ndarray):
         if not buf.flags.c_contiguous:
-            raise ValueError("host buffers must be contiguous")
+            raise ValueError("request buffers must be contiguous")
         return buf.ctypes.data, buf.nbytes
-    if buf.is_cuda or not buf.is_contiguous():
-        raise ValueError("host buffers must be contiguous CPU tensors")
+    if not buf.is_contiguous():
+        raise ValueError("request buffers must be contiguous tensors")
     return buf.data_ptr(), buf.numel() * buf.element_size()
 
 
@@ -391,15 +392,16 @@ def polar_server_create(batch: PolarBatch, reqs: np.ndarray, host_llr, host_out,
                         device_budget_bytes: int, max_frames: int, slots: int,
                         flags: int = 0) -> PolarServer:
     """Serving loop over `batch`. reqs: REQUEST_DTYPE array (circular, capacity =
-    len); host_llr / host_out: host buffers (pinned CPU tensors for overlap);
+    len); host_llr / host_out: pinned CPU tensors (or CUDA tensors: copies stay
+    on the device);
     done_ns: uint64 array of len(reqs) receiving completion times; flags:
     SERVE_LAUNCH_PER_CODE for one launch per code in each admission."""
     if reqs.dtype != REQUEST_DTYPE or not reqs.flags.c_contiguous:
         raise TypeError("reqs must be a contiguous REQUEST_DTYPE array")
     if done_ns.dtype != np.uint64 or done_ns.size != reqs.size or not done_ns.flags.c_contiguous:
         raise TypeError("done_ns must be a contiguous uint64 array of len(reqs) entries")
-    lp, lb = _host_ptr(host_llr)
-    op, ob = _host_ptr(host_out)
+    lp, lb = _buf_ptr(host_llr)
+    op, ob = _buf_ptr(host_out)
     h = ctypes.c_void_p()
     _check(_lib.polar_server_create(batch.handle, ctypes.c_void_p(reqs.ctypes.data), reqs.size,
                                     ctypes.c_void_p(lp), lb, ctypes.c_void_p(op), ob,

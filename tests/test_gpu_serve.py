@@ -144,6 +144,26 @@ def test_per_code_launch_policy(setup):
         assert np.array_equal(out[o: o + (K + 7) // 8], expected(masks, reqs, llrs, i)), i
 
 
+def test_device_resident_pool(setup):
+    """Request buffers in device memory (the copies stay in HBM) give the same
+    bits as the oracle."""
+    masks, batch = setup
+    n = 150
+    reqs, host_llr, host_out, llrs = make_requests(masks, n, 21)
+    d_llr = host_llr.cuda()
+    d_out = torch.zeros_like(host_out, device="cuda")
+    done = np.zeros(n, np.uint64)
+    srv = polar.polar_server_create(batch, reqs, d_llr, d_out, done, 1 << 26, 32, 3)
+    polar.polar_server_publish(srv, n)
+    drain(srv, n)
+    polar.polar_server_destroy(srv)
+    out = d_out.cpu().numpy()
+    for i in range(n):
+        K = CODES[reqs["code_id"][i]][1]
+        o = int(reqs["out_off"][i])
+        assert np.array_equal(out[o: o + (K + 7) // 8], expected(masks, reqs, llrs, i)), i
+
+
 def test_request_ring_wraps(setup):
     """A request array shorter than the run: slots are reused once complete."""
     masks, batch = setup
