@@ -355,14 +355,9 @@ def run_native(args, world, rank, local):
         """Code handle with its specialised decoder compiled (untimed set-up)."""
         i8 = dtype == "i8"
         code = polar.polar_code_create(N, K, mask)
-        shape = TUNED.get((args.workload, dtype))
-        tuned, src = tuned_or(N, K, mask, dtype, {})
-        if src == "tuned":  # the autotuner's table for this GPU
-            shape = dict(tuned, stage_channel=2)
-        if shape:
-            polar.polar_code_set_launch(code, i8, **shape)
-        if not args.interpreter:
-            polar.polar_code_compile(code, i8, batch)
+        shape, _ = tuned_or(N, K, mask, dtype, TUNED.get((args.workload, dtype), {}))
+        shape.setdefault("stage_channel", 2)
+        compile_shape(code, dtype, shape, batch, args.interpreter)
         return code
 
     def throughput(dtype, steps, warmup):
@@ -440,10 +435,8 @@ def run_native(args, world, rank, local):
     if nlat:
         i8 = main == "i8"
         lcode = polar.polar_code_create(N, K, mask)
-        if args.workload in TUNED_LATENCY:
-            polar.polar_code_set_launch(lcode, i8, **TUNED_LATENCY[args.workload])
-        if not args.interpreter:
-            polar.polar_code_compile(lcode, i8, 1)
+        lshape, _ = tuned_or(N, K, mask, main, TUNED_LATENCY.get(args.workload, {}), latency=True)
+        compile_shape(lcode, main, lshape, 1, args.interpreter)
         one_in = torch.empty((1, N), dtype=r["bufs"][0].dtype, device=dev)
         one_out = torch.empty((1, row), dtype=torch.uint8, device=dev)
         h1 = torch.empty((1, row), dtype=torch.uint8).pin_memory()
@@ -557,15 +550,29 @@ def mixed_inputs(n, dtype, seed, ebn0=None, ebn0_range=None):
     return masks, cid, llr, bits
 
 
-def tuned_or(N, K, mask, dtype, default):
+def tuned_or(N, K, mask, dtype, default, latency=False):
+    """Launch shape from the autotuner's table for this GPU, else `default`."""
     from paper_1504_00353_gb300 import autotune
     try:
-        e = autotune.lookup(N, K, mask, dtype)
+        e = autotune.lookup(N, K, mask, dtype, latency=latency)
     except Exception:  # no table or no device name
         e = None
     if not e:
         return dict(default), "default"
-    return {k: e[k] for k in ("threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm")}, "tuned"
+    return {k: e[k] for k in autotune.SHAPE_KEYS if k in e}, "tuned"
+
+
+def compile_shape(code, dtype, shape, n_frames, interpreter=False):
+    """Set a launch shape (dict of polar_code_set_launch arguments, plus
+    reg_subtree) and compile the specialised decoder unless timing the
+    interpreter."""
+    from paper_1504_00353_gb300 import polar
+    sh = dict(shape)
+    reg = sh.pop("reg_subtree", 0)
+    if sh:
+        polar.polar_code_set_launch(code, dtype == "i8", **sh)
+    if not interpreter:
+        polar.polar_code_compile(code, dtype == "i8", n_frames, reg)
 
 
 def batch_shape(dtype):
@@ -605,9 +612,9 @@ def run_mixed(args):
         shape, src = tuned_or(N, K, masks[c], dtype,
                               dict(threads=32, smem_stage_max=512, warp_stage_max=2048,
                                    ctas_per_sm=0))
+        shape.setdefault("stage_channel", 2)
         code = polar.polar_code_create(N, K, masks[c])
-        polar.polar_code_set_launch(code, dtype == "i8", stage_channel=2, **shape)
-        polar.polar_code_compile(code, dtype == "i8", llr[c].shape[0])
+        compile_shape(code, dtype, shape, llr[c].shape[0])
         codes.append(code)
         shapes.append(dict(shape, source=src))
         bufs.append(torch.from_numpy(llr[c]).to(dev))

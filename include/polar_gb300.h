@@ -204,9 +204,11 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
  * device, for the launch shape a decode of n_frames frames of this LLR type
  * uses (is_i8 = 0 float32, 1 int8). Later decodes whose shape matches run it
  * instead of the operation-list interpreter; results are bit-identical.
- *   reg_subtree  subtrees of at most this many leaves (power of two, 32..512;
+ *   reg_subtree  subtrees of at most this many leaves (power of two, 32..1024;
  *                0 = 256) are decoded entirely in the registers of one warp.
- * n_frames = 0 releases every specialised decoder of that LLR type.
+ * n_frames = 0 releases every specialised decoder of that LLR type. A decoder
+ * already compiled for the same launch shape is kept (release first to build
+ * one with another reg_subtree).
  * Blocking; takes seconds for long codes. Call before any stream capture.
  * Returns POLAR_ECUDA if NVRTC is unavailable or compilation fails (see
  * polar_code_compile_log); decodes then keep using the interpreter. */

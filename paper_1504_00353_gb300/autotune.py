@@ -42,8 +42,8 @@ def mask_hash(mask) -> str:
     return hashlib.sha1(np.ascontiguousarray(np.asarray(mask, np.uint8)).tobytes()).hexdigest()[:12]
 
 
-def code_key(N: int, K: int, mask, dtype: str) -> str:
-    return f"{N}_{K}_{mask_hash(mask)}_{dtype}"
+def code_key(N: int, K: int, mask, dtype: str, latency: bool = False) -> str:
+    return f"{N}_{K}_{mask_hash(mask)}_{dtype}" + ("_lat" if latency else "")
 
 
 def device_name() -> str:
@@ -66,16 +66,20 @@ def save_table(table: dict, path: str = TABLE):
     os.replace(tmp, path)
 
 
-def lookup(N: int, K: int, mask, dtype: str, table: dict | None = None, device: str | None = None):
-    """Tuned shape for a code, or None. Exact mask first, then same (N, K, dtype)."""
+def lookup(N: int, K: int, mask, dtype: str, table: dict | None = None, device: str | None = None,
+           latency: bool = False):
+    """Tuned shape for a code (batch-1 shape with latency=True), or None. Exact
+    mask first, then the same (N, K, dtype)."""
     table = load_table() if table is None else table
     dev = table.get(device or device_name(), {})
-    hit = dev.get(code_key(N, K, mask, dtype))
+    hit = dev.get(code_key(N, K, mask, dtype, latency))
     if hit:
         return hit
+    want = 5 if latency else 4
     for k, v in sorted(dev.items()):
         parts = k.split("_")
-        if len(parts) == 4 and parts[0] == str(N) and parts[1] == str(K) and parts[3] == dtype:
+        if (len(parts) == want and parts[0] == str(N) and parts[1] == str(K) and parts[3] == dtype
+                and (not latency or parts[4] == "lat")):
             return v
     return None
 
@@ -98,18 +102,33 @@ def frames_for(N: int, sms: int) -> int:
     return int(max(sms * 48, min(1 << 17, (1 << 26) // N)))
 
 
+SHAPE_KEYS = ("threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm", "stage_channel",
+              "reg_subtree")
+SHAPE_DEFAULTS = dict(ctas_per_sm=0, stage_channel=2, reg_subtree=256)
+
+
 def _shape_key(s: dict) -> tuple:
-    return (s["threads"], s["smem_stage_max"], s["warp_stage_max"], s.get("ctas_per_sm", 0))
+    return tuple(s.get(k, SHAPE_DEFAULTS.get(k, 0)) for k in SHAPE_KEYS)
+
+
+def _shape(key: tuple) -> dict:
+    return dict(zip(SHAPE_KEYS, key))
+
+
+def apply_shape(code, dtype: str, shape: dict, n_frames: int):
+    """Set a tuned shape on a code and compile its specialised decoder."""
+    sh = dict(SHAPE_DEFAULTS, **shape)
+    polar.polar_code_set_launch(code, dtype == "i8", threads=sh["threads"],
+                                smem_stage_max=sh["smem_stage_max"],
+                                warp_stage_max=sh["warp_stage_max"],
+                                ctas_per_sm=sh["ctas_per_sm"], stage_channel=sh["stage_channel"])
+    polar.polar_code_compile(code, dtype == "i8", n_frames, sh["reg_subtree"])
 
 
 def _compile(N, K, mask, dtype, shape, n_frames):
     code = polar.polar_code_create(N, K, mask)
-    polar.polar_code_set_launch(code, dtype == "i8", threads=shape["threads"],
-                                smem_stage_max=shape["smem_stage_max"],
-                                warp_stage_max=shape["warp_stage_max"],
-                                ctas_per_sm=shape.get("ctas_per_sm", 0), stage_channel=2)
     try:
-        polar.polar_code_compile(code, dtype == "i8", n_frames)
+        apply_shape(code, dtype, shape, n_frames)
     except polar.PolarError:
         return None
     return code
@@ -126,6 +145,25 @@ def _warm(fn, seconds=0.05):
         fn()
         torch.cuda.synchronize()
         k += 1
+
+
+def _time_latency(code, dtype, llr, out, reps=30) -> float:
+    """Device time of a one-frame decode, queued behind a spin so that the host
+    call overhead is not inside the events (median of reps)."""
+    import torch
+    dec = polar.polar_decode_i8 if dtype == "i8" else polar.polar_decode
+    one_in, one_out = llr[:1], out[:1]
+    _warm(lambda: dec(code, one_in, one_out), 0.02)
+    ts = []
+    for _ in range(reps):
+        torch.cuda._sleep(200_000)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dec(code, one_in, one_out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    return statistics.median(ts)
 
 
 def _time(code, dtype, llr, out, reps=5) -> float:
@@ -146,11 +184,13 @@ def _time(code, dtype, llr, out, reps=5) -> float:
 class CodeTuner:
     """Times launch shapes of one code; remembers every shape it measured."""
 
-    def __init__(self, N, K, mask, dtype, ebn0_db=3.0, n_frames=None, workers=8, log=None):
+    def __init__(self, N, K, mask, dtype, ebn0_db=3.0, n_frames=None, workers=8, log=None,
+                 latency=False):
         import torch
         self.N, self.K, self.mask, self.dtype = N, K, np.asarray(mask, np.uint8), dtype
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        self.n_frames = n_frames or frames_for(N, sms)
+        self.latency = latency
+        self.n_frames = 1 if latency else (n_frames or frames_for(N, sms))
         self.llr = synthetic_llr(N, self.n_frames, dtype, ebn0_db, K / N)
         self.out = torch.empty((self.n_frames, (K + 7) // 8), dtype=torch.uint8, device="cuda")
         self.workers = workers
@@ -159,9 +199,11 @@ class CodeTuner:
 
     def clamp(self, s) -> dict:
         """The shape the library would use: stage cap at most N/2, warp threshold
-        at most N (larger values change nothing)."""
+        at most N, register subtree at most N (larger values change nothing)."""
+        s = dict(SHAPE_DEFAULTS, **s)
         return dict(s, smem_stage_max=min(s["smem_stage_max"], max(self.N // 2, 64)),
-                    warp_stage_max=min(s["warp_stage_max"], max(self.N, 256)))
+                    warp_stage_max=min(s["warp_stage_max"], max(self.N, 256)),
+                    reg_subtree=max(32, min(s["reg_subtree"], self.N)))
 
     def measure(self, shapes) -> None:
         todo = []
@@ -178,18 +220,37 @@ class CodeTuner:
                 self.seen[_shape_key(s)] = float("inf")
                 continue
             launch = polar.polar_code_get_launch(code, self.dtype == "i8", self.n_frames)
-            t = _time(code, self.dtype, self.llr, self.out) / self.n_frames if launch["unrolled"] \
-                else float("inf")
+            if not launch["unrolled"]:
+                t = float("inf")
+            elif self.latency:
+                t = _time_latency(code, self.dtype, self.llr, self.out)
+            else:
+                t = _time(code, self.dtype, self.llr, self.out) / self.n_frames
             self.seen[_shape_key(s)] = t
             if self.log:
-                self.log(f"  ({self.N},{self.K}) {self.dtype} {_shape_key(s)}: "
-                         f"{self.K / t / 1e9 if t < float('inf') else 0:.1f} Gbps")
+                what = (f"{t * 1e6:.1f} us" if self.latency else
+                        f"{self.K / t / 1e9 if t < float('inf') else 0:.1f} Gbps")
+                self.log(f"  ({self.N},{self.K}) {self.dtype} {_shape_key(s)}: {what}")
             del code
 
     def best(self, threads=None) -> tuple[dict, float]:
         cands = [(t, k) for k, t in self.seen.items() if threads is None or k[0] == threads]
         t, k = min(cands)
-        return dict(threads=k[0], smem_stage_max=k[1], warp_stage_max=k[2], ctas_per_sm=k[3]), t
+        return _shape(k), t
+
+    def tune_latency(self) -> tuple[dict, float]:
+        """Batch-1 shape: one CTA, every stage in shared memory when it fits
+        (stage cap 0 = the library's choice), register subtrees up to 1024 leaves."""
+        base = dict(smem_stage_max=0, warp_stage_max=1024, ctas_per_sm=0, stage_channel=1,
+                    reg_subtree=256)
+        self.measure([dict(base, threads=t) for t in (128, 256, 512, 1024)])
+        cur, _ = self.best()
+        self.measure([dict(cur, warp_stage_max=w) for w in (256, 512, 1024, 2048, 4096)])
+        cur, _ = self.best()
+        self.measure([dict(cur, reg_subtree=r) for r in (256, 512, 1024)])
+        cur, _ = self.best()
+        self.measure([dict(cur, stage_channel=c) for c in (1, 2)])
+        return self.best()
 
     def tune(self, threads_options=THREADS, fixed_threads=None, tune_ctas=True) -> tuple[dict, float]:
         def default(t):
@@ -214,13 +275,18 @@ class CodeTuner:
 
 
 def tune_code(N, K, mask, dtype, table=None, save=True, tuner=None, **kw) -> dict:
-    """Tune one code; store and return its entry."""
+    """Tune one code (throughput, or batch-1 with latency=True); store and return
+    its entry."""
     tuner = tuner or CodeTuner(N, K, mask, dtype, **kw)
-    shape, t = tuner.tune()
-    entry = dict(shape, gbps=K / t / 1e9, n_frames=tuner.n_frames)
+    if tuner.latency:
+        shape, t = tuner.tune_latency()
+        entry = dict(shape, latency_us=t * 1e6, n_frames=1)
+    else:
+        shape, t = tuner.tune()
+        entry = dict(shape, gbps=K / t / 1e9, n_frames=tuner.n_frames)
     with _lock:
         tab = load_table() if table is None else table
-        tab.setdefault(device_name(), {})[code_key(N, K, mask, dtype)] = entry
+        tab.setdefault(device_name(), {})[code_key(N, K, mask, dtype, tuner.latency)] = entry
         if save:
             save_table(tab)
     return entry
@@ -331,6 +397,8 @@ def main(argv=None):
                    help="a named workload of synth.WORKLOADS (repeatable)")
     p.add_argument("--mixed", action="store_true", help="the mixed-length code set")
     p.add_argument("--dtype", action="append", default=[], choices=["f32", "i8"])
+    p.add_argument("--latency", action="store_true",
+                   help="tune the batch-1 (latency) shape of the named workloads instead")
     p.add_argument("--out", default=TABLE)
     a = p.parse_args(argv)
     torch.cuda.set_device(0)
@@ -344,12 +412,13 @@ def main(argv=None):
     for dtype in a.dtype or ["i8"]:
         tuners = []
         for N, K, mask, db, nf in codes:
-            tu = CodeTuner(N, K, mask, dtype, ebn0_db=db, n_frames=nf, log=print)
+            tu = CodeTuner(N, K, mask, dtype, ebn0_db=db, n_frames=nf, log=print,
+                           latency=a.latency)
             e = tune_code(N, K, mask, dtype, table=table, save=False, tuner=tu)
             print(f"({N},{K}) {dtype}: {e}", flush=True)
             save_table(table, a.out)
             tuners.append((db, tu))
-        if a.mixed:
+        if a.mixed and not a.latency:
             mixed = [tu for db, tu in tuners if db == synth.MIXED_DESIGN_DB and
                      (tu.N, tu.K) in synth.MIXED_CODES][-len(synth.MIXED_CODES):]
             b = tune_batch(mixed, log=print)

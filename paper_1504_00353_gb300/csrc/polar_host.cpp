@@ -577,7 +577,7 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
                                 uint32_t reg_subtree) {
     if (!code) return POLAR_EINVAL;
     if (reg_subtree == 0) reg_subtree = 256;
-    if (!is_pow2(reg_subtree) || reg_subtree < 32 || reg_subtree > 512) return POLAR_EINVAL;
+    if (!is_pow2(reg_subtree) || reg_subtree < 32 || reg_subtree > 1024) return POLAR_EINVAL;
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();

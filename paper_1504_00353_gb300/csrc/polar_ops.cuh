@@ -771,13 +771,14 @@ template <typename T, uint32_t R>
 struct RegSub {
     using Acc = typename Llr<T>::Acc;
     static constexpr uint32_t NWORD = R >= 32 ? R / 32 : 1;
-    Acc s512[16], s256[8], s128[4], s64[2], s32, A;
+    Acc s1024[32], s512[16], s256[8], s128[4], s64[2], s32, A;
     uint32_t bw[NWORD];
     uint32_t lane;
 
     template <uint32_t m, uint32_t k>
     __device__ __forceinline__ Acc &reg() {
-        if constexpr (m == 512) return s512[k];
+        if constexpr (m == 1024) return s1024[k];
+        else if constexpr (m == 512) return s512[k];
         else if constexpr (m == 256) return s256[k];
         else if constexpr (m == 128) return s128[k];
         else if constexpr (m == 64) return s64[k];

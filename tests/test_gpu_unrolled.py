@@ -40,7 +40,8 @@ def test_n1024_unrolled(i8, n_frames):
     assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y))
 
 
-@pytest.mark.parametrize("N,reg", [(8, 32), (64, 64), (512, 256), (4096, 512), (2048, 32)])
+@pytest.mark.parametrize("N,reg", [(8, 32), (64, 64), (512, 256), (4096, 512), (2048, 32),
+                                   (8192, 1024)])
 def test_random_masks_unrolled(N, reg):
     rng = np.random.default_rng(N + reg)
     K = int(rng.integers(1, N))
@@ -67,6 +68,21 @@ def test_n32768_unrolled_batch4096_sampled(i8):
     polar.polar_code_compile(code, i8, 1)
     one = decode(code, y[:1], i8)
     assert np.array_equal(one, oracle.decode_batch(mask, y[:1]))
+
+
+@pytest.mark.parametrize("i8", [False, True])
+@pytest.mark.parametrize("threads,reg,stage", [(256, 1024, 1), (512, 512, 2)])
+def test_n32768_batch1_shapes(i8, threads, reg, stage):
+    """Batch-1 (latency) shapes: one CTA, every stage in shared memory, register
+    subtrees of 512 and 1024 leaves, staged or in-place channel."""
+    mask, d, llr = _cases.frames(32768, 29492, 4.0, 3, seed=33)
+    y = synth.quantize_i8(llr) if i8 else llr
+    code = polar.polar_code_create(32768, 29492, mask)
+    polar.polar_code_set_launch(code, i8, threads=threads, warp_stage_max=1024, stage_channel=stage)
+    polar.polar_code_compile(code, i8, 1, reg)
+    assert polar.polar_code_get_launch(code, i8, 1)["unrolled"] == reg
+    for f in range(3):
+        assert np.array_equal(decode(code, y[f:f + 1], i8), oracle.decode_batch(mask, y[f:f + 1]))
 
 
 def test_release_returns_to_interpreter():
