@@ -96,6 +96,8 @@ def lib():
             L.oracle_f_i8.restype = ctypes.c_int8
             L.oracle_g_i8.argtypes = [ctypes.c_int8, ctypes.c_int8, ctypes.c_uint8]
             L.oracle_g_i8.restype = ctypes.c_int8
+            L.oracle_repspc_f32.argtypes = [fp, u32, u8p]
+            L.oracle_repspc_i8.argtypes = [i8p, u32, u8p]
             _lib = L
         return _lib
 
@@ -241,3 +243,19 @@ def f_i8(a, b):
 
 def g_i8(a, b, beta):
     return lib().oracle_g_i8(a, b, beta)
+
+
+def repspc(llr) -> np.ndarray:
+    """Speculative Repetition-SPC node decode (Sec. II-D) of one node's LLRs
+    (float32, or int8 for the saturating decoder): its n estimates."""
+    n = np.asarray(llr).size
+    beta = np.empty(n, dtype=np.uint8)
+    if np.asarray(llr).dtype == np.int8:
+        y = np.ascontiguousarray(llr, dtype=np.int8)
+        rc = lib().oracle_repspc_i8(_p(y, ctypes.c_int8), n, _p(beta, ctypes.c_uint8))
+    else:
+        y = np.ascontiguousarray(llr, dtype=np.float32)
+        rc = lib().oracle_repspc_f32(_p(y, ctypes.c_float), n, _p(beta, ctypes.c_uint8))
+    if rc != 0:
+        raise RuntimeError(f"oracle Repetition-SPC failed: {rc}")
+    return beta

@@ -373,6 +373,73 @@ int oracle_fastssc_decode_i8(uint32_t N, const uint8_t *frozen, const int8_t *ll
 }
 
 /* ------------------------------------------------------------------ */
+/* Repetition-SPC node                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Repetition-SPC node (Sec. II-D, "Repetition-SPC codes"): a node of n leaves
+ * whose left child is a Repetition code and whose right child is an SPC code,
+ * decoded speculatively. Three decodes are independent of one another: the
+ * Repetition child on F of the node's LLRs (Eq. 1), and the SPC child on the
+ * G outputs (Eq. 2) for a left estimate of all zeros and for one of all ones.
+ * The Repetition decision then selects the matching SPC estimate, and Eq. 3
+ * joins the halves. n is a power of two, 8 <= n. */
+static int repspc_node(const float *a, uint32_t n, uint8_t *beta, int sat)
+{
+    uint32_t h = n / 2;
+    float *buf = (float *)malloc(sizeof(float) * 4 * h);
+    uint8_t *spc = (uint8_t *)malloc(2 * h);
+    if (!buf || !spc) {
+        free(buf);
+        free(spc);
+        return -1;
+    }
+    float *fl = buf, *g0 = buf + h, *g1 = buf + 2 * h, *work = buf + 3 * h;
+    uint8_t rep[1];
+    for (uint32_t i = 0; i < h; i++) {
+        fl[i] = f_op(a[i], a[i + h]);
+        g0[i] = g_op(a[i], a[i + h], 0, sat); /* left estimate all 0 */
+        g1[i] = g_op(a[i], a[i + h], 1, sat); /* left estimate all 1 */
+    }
+    /* the Repetition decision is the same bit for every leaf of the left half */
+    uint8_t *left = (uint8_t *)malloc(h);
+    if (!left) {
+        free(buf);
+        free(spc);
+        return -1;
+    }
+    rep_node(fl, h, left, work, sat);
+    rep[0] = left[0];
+    spc_node(g0, h, spc);
+    spc_node(g1, h, spc + h);
+    const uint8_t *right = rep[0] ? spc + h : spc;
+    for (uint32_t i = 0; i < h; i++) {
+        beta[i] = left[i] ^ right[i]; /* Eq. 3 */
+        beta[i + h] = right[i];
+    }
+    free(left);
+    free(buf);
+    free(spc);
+    return 0;
+}
+
+int oracle_repspc_f32(const float *alpha, uint32_t n, uint8_t *beta)
+{
+    if (!is_pow2(n) || n < 8) return -1;
+    return repspc_node(alpha, n, beta, 0);
+}
+
+int oracle_repspc_i8(const int8_t *alpha, uint32_t n, uint8_t *beta)
+{
+    if (!is_pow2(n) || n < 8) return -1;
+    float *a = (float *)malloc(sizeof(float) * n);
+    if (!a) return -1;
+    for (uint32_t i = 0; i < n; i++) a[i] = (float)alpha[i];
+    int rc = repspc_node(a, n, beta, 1);
+    free(a);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
 /* Batches                                                             */
 /* ------------------------------------------------------------------ */
 

@@ -100,6 +100,12 @@ int oracle_decode_batch_i8(uint32_t N, const uint8_t *frozen, const int8_t *llr,
 /* Single-element operations, exposed for unit pins.
  * f: Eq. 1 (min-sum); g: Eq. 2; the int8 forms saturate to [-127, 127]
  * (Sec. III-A: only G grows the amplitude and uses saturating adders). */
+/* Repetition-SPC node decoded speculatively (Sec. II-D): n LLRs of a node whose
+ * left child is a Repetition code and right child an SPC code (n a power of
+ * two, n >= 8) -> its n estimates. Returns 0, or -1 for a bad n. */
+int oracle_repspc_f32(const float *alpha, uint32_t n, uint8_t *beta);
+int oracle_repspc_i8(const int8_t *alpha, uint32_t n, uint8_t *beta);
+
 float oracle_f_f32(float a, float b);
 float oracle_g_f32(float a, float b, uint8_t beta_l);
 int8_t oracle_f_i8(int8_t a, int8_t b);

@@ -313,3 +313,46 @@ def test_batch_decode_matches_single():
         assert np.array_equal(out[f], oracle.extract_info(mask, oracle.fastssc_decode(mask, llr[f])))
     assert np.array_equal(oracle.decode_batch(mask, llr, algo="sc")[3],
                           oracle.extract_info(mask, oracle.sc_decode(mask, llr[3])))
+
+
+def _repspc_mask(n):
+    """Node of n leaves: left half a Repetition code (only its last leaf carries
+    information), right half an SPC code (only its first leaf frozen)."""
+    h = n // 2
+    m = np.zeros(n, np.uint8)
+    m[: h - 1] = 1
+    m[h] = 1
+    return m
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+def test_repspc_speculative_equals_sequential(n):
+    """Sec. II-D: the speculative Repetition-SPC decode (Repetition and two SPC
+    hypotheses in parallel, then a selection) gives what the plain Fast-SSC
+    order F, Repetition, G, SPC, Combine gives on the same node, for float32
+    and for saturating int8 LLRs (ties and +-127 included); both Repetition
+    outcomes occur in the sample, so a swapped selection would fail."""
+    mask = _repspc_mask(n)
+    rng = np.random.default_rng(n)
+    _, ops, _ = oracle.fastssc_decode(mask, rng.standard_normal(n).astype(np.float32), trace=True)
+    assert [o[0] for o in ops] == ["F", "Rep", "G", "SPC", "Combine"]
+    reps = set()
+    for t in range(400):
+        if t % 2:
+            y = rng.integers(-127, 128, n).astype(np.int8)
+            if t % 4 == 1:
+                y[rng.integers(0, n, 3)] = rng.choice([-127, 127, 0], 3).astype(np.int8)
+        else:
+            y = (rng.standard_normal(n) * 2 + rng.choice([-1, 1])).astype(np.float32)
+        got = oracle.repspc(y)
+        assert np.array_equal(got, oracle.fastssc_decode(mask, y)), (n, t)
+        reps.add(int(got[0] ^ got[n // 2]))  # left = decision XOR right (Eq. 3)
+        assert not oracle.encode(got)[mask == 1].any()  # a codeword of the node's code
+    assert len(reps) == 2
+
+
+def test_repspc_rejects_bad_size():
+    with pytest.raises(RuntimeError):
+        oracle.repspc(np.zeros(4, np.float32))
+    with pytest.raises(RuntimeError):
+        oracle.repspc(np.zeros(12, np.float32))
