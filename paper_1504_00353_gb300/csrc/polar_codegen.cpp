@@ -140,6 +140,23 @@ namespace {
 // struct <name> { operator()(frame) }: the code's operation list with every
 // node size and offset written as a constant. S = shared-memory stage cap,
 // W = widest node run on warp 0 alone, R = largest register-resident subtree.
+// ops[i..i+4] are F, Repetition, G, SPC, Combine of one node of 8 or 16 leaves,
+// all inside one register subtree (Sec. II-D, "Repetition-SPC codes").
+bool is_repspc(const std::vector<HostOp> &ops, size_t i) {
+    if (i + 4 >= ops.size()) return false;
+    const HostOp &f = ops[i], &r = ops[i + 1], &g = ops[i + 2], &s = ops[i + 3], &c = ops[i + 4];
+    const uint32_t l = f.log2n;
+    if (f.kind != OP_F || (l != 3 && l != 4)) return false;
+    for (size_t k = i; k <= i + 4; ++k) {
+        if (!(ops[k].flags & OPW_REG)) return false;
+        if (k > i && (ops[k].flags & OPW_REG_ENTER)) return false;
+        if (k < i + 4 && (ops[k].flags & OPW_REG_EXIT)) return false;
+    }
+    return r.kind == OP_REP && r.log2n == l - 1 && r.off == f.off && g.kind == OP_G &&
+           g.log2n == l && g.off == f.off && s.kind == OP_SPC && s.log2n == l - 1 &&
+           s.off == f.off + (1u << (l - 1)) && c.kind == OP_C && c.log2n == l && c.off == f.off;
+}
+
 void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
                uint32_t R, const std::string &name) {
     const uint32_t N = code.N;
@@ -228,6 +245,15 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
               << "        r.template enter<" << n0 << "u>(" << in(n0) << ");\n";
         }
         const uint32_t p = op.off - o0;
+        if (is_repspc(ops, i)) {  // F, rep, G, spc, combine of one 8- or 16-leaf node
+            o << "        r.template repspc<" << n << "u, " << p << "u>();\n";
+            i += 4;
+            if (ops[i].flags & OPW_REG_EXIT) {
+                o << "        r.template exit<" << n0 << "u>(fr.beta, " << o0 << "u);\n      }\n"
+                  << "      __syncwarp();\n";
+            }
+            continue;
+        }
         o << "        r.template ";
         switch (op.kind) {
         case OP_F:

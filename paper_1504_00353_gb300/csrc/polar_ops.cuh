@@ -941,6 +941,40 @@ struct RegSub {
         }
     }
 
+    // Repetition-SPC node of n leaves (8 or 16) at subtree offset p, decoded
+    // speculatively (Sec. II-D): F feeds the Repetition child while G for a
+    // left estimate of all zeros and for one of all ones feed two SPC decodes;
+    // the Repetition decision selects one SPC estimate and Eq. 3 joins the
+    // halves. Bit-identical to F, rep, G, spc, combine in that order (the fold
+    // order of the sum and the SPC tie rule are the ones rep<> and spc<> use).
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void repspc() {
+        static_assert(n == 8 || n == 16, "Repetition-SPC node in the shuffle layout");
+        constexpr uint32_t h = n / 2;
+        const bool act = lane < h;
+        const Acc x = __shfl_sync(kFull, A, (n + lane) & 31u);      // alpha_v[i], i = lane
+        const Acc y = __shfl_sync(kFull, A, (n + h + lane) & 31u);  // alpha_v[i + h]
+        Acc s = op_f(x, y);
+#pragma unroll
+        for (uint32_t m = h / 2; m >= 1; m /= 2) {
+            const Acc t = __shfl_down_sync(kFull, s, m);
+            if (lane < m) s = op_add(s, t);
+        }
+        const bool one = __shfl_sync(kFull, s, 0) < Acc(0);
+        const Acc g0 = op_g(x, y, 0u), g1 = op_g(x, y, 1u);
+        const uint32_t hd0 = __ballot_sync(kFull, act && g0 < Acc(0));
+        const uint32_t hd1 = __ballot_sync(kFull, act && g1 < Acc(0));
+        const uint32_t m0 = act ? mag_bits(g0) : kFull, m1 = act ? mag_bits(g1) : kFull;
+        const uint32_t mn0 = __reduce_min_sync(kFull, m0), mn1 = __reduce_min_sync(kFull, m1);
+        const uint32_t f0 = __ffs(__ballot_sync(kFull, act && m0 == mn0)) - 1u;
+        const uint32_t f1 = __ffs(__ballot_sync(kFull, act && m1 == mn1)) - 1u;
+        const uint32_t r0 = hd0 ^ ((__popc(hd0) & 1u) << f0);
+        const uint32_t r1 = hd1 ^ ((__popc(hd1) & 1u) << f1);
+        const uint32_t right = one ? r1 : r0;
+        const uint32_t left = (one ? (1u << h) - 1u : 0u) ^ right;
+        set_field<p / 32, p % 32, n>(left | (right << h));
+    }
+
     template <uint32_t n, uint32_t p>
     __device__ __forceinline__ void spc() {
         if constexpr (n >= 32) {

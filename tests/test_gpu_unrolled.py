@@ -85,6 +85,36 @@ def test_n32768_batch1_shapes(i8, threads, reg, stage):
         assert np.array_equal(decode(code, y[f:f + 1], i8), oracle.decode_batch(mask, y[f:f + 1]))
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_repspc_heavy_masks(seed):
+    """Masks built from Repetition-SPC nodes of 8 and 16 leaves (decoded by the
+    speculative register op) among random blocks: bits equal the oracle's."""
+    rng = np.random.default_rng(40 + seed)
+
+    def repspc(n):
+        m = np.zeros(n, np.uint8)
+        m[: n // 2 - 1] = 1
+        m[n // 2] = 1
+        return m
+    blocks = []
+    for _ in range(64):
+        c = int(rng.integers(0, 3))
+        blocks.append(repspc(16) if c == 0 else np.concatenate([repspc(8), repspc(8)]) if c == 1
+                      else (rng.random(16) < 0.5).astype(np.uint8))
+    mask = np.concatenate(blocks)
+    N, K = mask.size, int((mask == 0).sum())
+    code = polar.polar_code_create(N, K, mask)
+    y32 = (rng.standard_normal((300, N)) * 2 + 1).astype(np.float32)
+    yi = rng.integers(-127, 128, (300, N)).astype(np.int8)
+    yi[:, ::7] = 127
+    for y, i8 in ((y32, False), (yi, True)):
+        for reg in (32, 256):
+            c = polar.polar_code_create(N, K, mask)
+            polar.polar_code_compile(c, i8, 300, reg)
+            assert polar.polar_code_get_launch(c, i8, 300)["unrolled"] == reg
+            assert np.array_equal(decode(c, y, i8), oracle.decode_batch(mask, y))
+
+
 def test_release_returns_to_interpreter():
     mask, d, llr = _cases.frames(256, 128, 3.0, 50, seed=32)
     code = polar.polar_code_create(256, 128, mask)
