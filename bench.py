@@ -56,10 +56,11 @@ def parse():
     p.add_argument("--no-variant", action="store_true", help="skip the other LLR type")
     p.add_argument("--interpreter", action="store_true",
                    help="time the operation-list interpreter instead of the specialised decoder")
-    p.add_argument("--mode", choices=["throughput", "mixed", "serve"], default="throughput",
+    p.add_argument("--mode", choices=["throughput", "mixed", "serve", "fer"], default="throughput",
                    help="throughput: one code, batch and batch-1 (default); mixed: 65,536 frames "
                         "of five codes, one persistent launch in a CUDA graph vs one launch per "
-                        "code; serve: Poisson arrivals through the serving loop vs a plain queue")
+                        "code; serve: Poisson arrivals through the serving loop vs a plain queue; "
+                        "fer: frame/bit error rates of float32 vs int8 from the GPU chain")
     p.add_argument("--loads", default="1,10,50,200", help="serve: offered loads, coded Gbps")
     p.add_argument("--serve-seconds", type=float, default=1.0,
                    help="serve: seconds of arrivals per load (at most --serve-max-frames)")
@@ -876,8 +877,56 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- error rates
+
+FER_POINTS = {
+    "n1024_k512_2.5db": ([1.0, 1.5, 2.0, 2.5, 3.0], 400_000),
+    "n32768_k29492_4.0db": ([3.75, 4.0, 4.25, 4.5, 4.75], 40_000),
+}
+
+
+def run_fer(args):
+    """Frame and bit error rates over BPSK-AWGN, float32 against int8 LLRs (x8,
+    +-127), every step on the GPU (Philox bits and noise, device encoder,
+    specialised decoder, error count)."""
+    import torch
+
+    from paper_1504_00353_gb300 import polar
+    torch.cuda.set_device(0)
+    rows = []
+    batch = 16384
+    for wl_name, (points, frames) in FER_POINTS.items():
+        wl = synth.WORKLOADS[wl_name]
+        N, K = wl["N"], wl["K"]
+        mask = synth.frozen_mask(N, K, wl["design_db"])
+        for dtype in ("f32", "i8"):
+            code = polar.polar_code_create(N, K, mask)
+            shape, _ = tuned_or(N, K, mask, dtype, {})
+            shape.setdefault("stage_channel", 2)
+            compile_shape(code, dtype, shape, batch)
+            polar.polar_fer_run(code, dtype == "i8", points[0], 0, batch, batch)  # warm-up
+            for db in points:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fe, be = polar.polar_fer_run(code, dtype == "i8", db, 2024, frames, batch)
+                dt = time.perf_counter() - t0
+                rows.append({"workload": wl_name, "llr": dtype, "ebn0_db": db, "frames": frames,
+                             "frame_errors": fe, "bit_errors": be, "fer": fe / frames,
+                             "ber": be / (frames * K), "seconds": dt,
+                             "chain_info_gbps": frames * K / dt / 1e9})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "frame / bit error rate, float32 vs int8 LLRs", "mode": "fer",
+            "data": "synthetic", "config": {"workloads": list(FER_POINTS), "batch": batch,
+                                            "channel": "BPSK-AWGN, Philox-4x32-10 + Box-Muller",
+                                            "seed": 2024},
+            "points": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "fer":
+        return run_fer(args)
     if args.mode == "mixed":
         return run_mixed(args)
     if args.mode == "serve":

@@ -353,6 +353,47 @@ polar_status polar_server_progress(const polar_server_t *server, uint64_t *n_com
  * free the server. Returns the loop's error status. */
 polar_status polar_server_destroy(polar_server_t *server);
 
+/* ---- Communication chain on the GPU (frame / bit error rates) ---- */
+
+/* Uniform random information bits: row f (ceil(K/8) bytes, device memory)
+ * from Philox-4x32-10 (Salmon et al., SC 2011) with key `seed` and counter
+ * (word, frame0 + f, stream 1); bits at and beyond K are 0. Asynchronous. */
+polar_status polar_random_info(const polar_code_t *code, uint8_t *info_packed, size_t n_frames,
+                               uint64_t seed, uint64_t frame0, polar_stream_t stream);
+
+/* Systematic encoding on the device (same result as polar_encode_systematic):
+ * info_packed [n][ceil(K/8)] -> codeword_packed [n][ceil(N/8)], device
+ * memory. POLAR_EINVAL if the frozen set is not one the two-step encoder
+ * handles (checked once per handle on the host). Asynchronous. */
+polar_status polar_encode_systematic_device(const polar_code_t *code, const uint8_t *info_packed,
+                                            uint8_t *codeword_packed, size_t n_frames,
+                                            polar_stream_t stream);
+
+/* BPSK (bit 0 -> +1) over AWGN at Eb/N0 = ebn0_db with rate K/N:
+ * sigma^2 = 1 / (2 R 10^(Eb/N0 / 10)), LLR = 2 y / sigma^2 written as float32
+ * [n][N] (is_i8 = 0) or int8 q = clamp(rint(8 LLR), -127, 127) (is_i8 = 1).
+ * Normals are Box-Muller pairs of Philox-4x32-10 words (key `seed`, counter
+ * (element / 4, frame0 + f, stream 2)). Device memory; asynchronous. */
+polar_status polar_channel_awgn(const polar_code_t *code, const uint8_t *codeword_packed,
+                                void *llr, int is_i8, size_t n_frames, float ebn0_db,
+                                uint64_t seed, uint64_t frame0, polar_stream_t stream);
+
+/* counters[0] += frames whose ceil(K/8)-byte rows of `decoded` and `sent`
+ * differ, counters[1] += differing bits. Device memory; asynchronous. */
+polar_status polar_count_errors(const polar_code_t *code, const uint8_t *decoded,
+                                const uint8_t *sent, size_t n_frames,
+                                unsigned long long *counters, polar_stream_t stream);
+
+/* Frame and bit errors of the decoder over n_frames frames at ebn0_db, run in
+ * batches of `batch` frames (0 = 16384) entirely on the current device:
+ * random information bits, systematic encoding, the AWGN channel, the decoder
+ * (the specialised decoder if one was compiled for the batch's shape) and the
+ * error count. Synchronous; the paper has no GPU chain (its error-rate
+ * figures come from a CPU simulation). */
+polar_status polar_fer_run(const polar_code_t *code, int is_i8, float ebn0_db, uint64_t seed,
+                           size_t n_frames, size_t batch, uint64_t *frame_errors,
+                           uint64_t *bit_errors);
+
 /* Wait for `stream`, then read and clear the handle's device status word on
  * the current device. POLAR_ETIMEOUT if a bounded device wait expired since
  * the last check, POLAR_OK otherwise. */

@@ -293,6 +293,12 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
 
 }  // namespace
 
+namespace polar {
+polar_status code_device_state(polar_code *c, int device, DeviceState **out) {
+    return ensure_device(c, device, out);
+}
+}  // namespace polar
+
 extern "C" {
 
 const char *polar_status_str(polar_status s) {

@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 
+#include "polar_gb300.h"
 #include "polar_ops.cuh"
 
 namespace polar {
@@ -111,6 +112,7 @@ struct polar_code {
     std::vector<polar::DeviceState> dev = std::vector<polar::DeviceState>(polar::kMaxDevices);
     std::map<polar::CompiledKey, polar::CompiledKernel> compiled;
     std::string compile_log;
+    bool systematic_checked = false, systematic_valid = false;  // device encoder check
 
     // Node type from its leaves, in this order: all frozen -> Rate-0, none
     // frozen -> Rate-1, only the last leaf information -> Repetition, only the
@@ -278,6 +280,9 @@ int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes);
 // Launch a compiled decoder on the current device.
 cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const void *args,
                             cudaStream_t stream);
+// The code's tables on `device` (uploaded on first use): op words, trace
+// offsets and the info-bit packing tables (see DeviceState).
+polar_status code_device_state(polar_code *c, int device, DeviceState **out);
 // Launch the batch decoder over n_frames frames with the given work counter and
 // alpha scratch (grid = min(resident CTAs, n_frames)); zeroes the counter on
 // the stream first. polar_batch_decode passes the batch's own workspace, the

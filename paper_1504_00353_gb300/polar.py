@@ -27,7 +27,8 @@ EXPORTS = [
     "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_log",
     "polar_decode_noalloc", "polar_batch_create", "polar_batch_destroy", "polar_batch_decode",
     "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
-    "polar_server_progress", "polar_server_destroy",
+    "polar_server_progress", "polar_server_destroy", "polar_random_info",
+    "polar_encode_systematic_device", "polar_channel_awgn", "polar_count_errors", "polar_fer_run",
 ]
 
 # struct polar_request
@@ -82,6 +83,13 @@ def _load():
                                    ctypes.POINTER(ctypes.c_uint64),
                                    ctypes.POINTER(ctypes.c_uint64)], st),
         "polar_server_destroy": ([vp], st),
+        "polar_random_info": ([vp, vp, sz, ctypes.c_uint64, ctypes.c_uint64, vp], st),
+        "polar_encode_systematic_device": ([vp, vp, vp, sz, vp], st),
+        "polar_channel_awgn": ([vp, vp, vp, st, sz, ctypes.c_float, ctypes.c_uint64,
+                                ctypes.c_uint64, vp], st),
+        "polar_count_errors": ([vp, vp, vp, sz, vp, vp], st),
+        "polar_fer_run": ([vp, st, ctypes.c_float, ctypes.c_uint64, sz, sz,
+                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -425,3 +433,55 @@ def polar_server_progress(server: PolarServer):
 
 def polar_server_destroy(server: PolarServer):
     _check(server.destroy(), "polar_server_destroy")
+
+
+# ---- communication chain on the GPU
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def polar_random_info(code: PolarCode, info_out, seed: int, frame0: int = 0, n_frames=None,
+                      stream=None):
+    """Fill a CUDA uint8 tensor [n, ceil(K/8)] with Philox information bits."""
+    n = info_out.numel() // max(code.out_row, 1) if n_frames is None else int(n_frames)
+    _check(_lib.polar_random_info(code.handle, _dptr(info_out), n, seed, frame0,
+                                  _stream_handle(stream)), "polar_random_info")
+    return info_out
+
+
+def polar_encode_systematic_device(code: PolarCode, info, codeword_out, n_frames=None, stream=None):
+    """Device systematic encoder: CUDA uint8 [n, ceil(K/8)] -> [n, ceil(N/8)]."""
+    n = info.numel() // max(code.out_row, 1) if n_frames is None else int(n_frames)
+    _check(_lib.polar_encode_systematic_device(code.handle, _dptr(info), _dptr(codeword_out), n,
+                                               _stream_handle(stream)),
+           "polar_encode_systematic_device")
+    return codeword_out
+
+
+def polar_channel_awgn(code: PolarCode, codewords, llr_out, ebn0_db: float, seed: int,
+                       frame0: int = 0, n_frames=None, stream=None):
+    """BPSK-AWGN channel LLRs into llr_out (CUDA float32 or int8 [n, N])."""
+    import torch
+    n = llr_out.numel() // code.N if n_frames is None else int(n_frames)
+    _check(_lib.polar_channel_awgn(code.handle, _dptr(codewords), _dptr(llr_out),
+                                   1 if llr_out.dtype == torch.int8 else 0, n, ebn0_db, seed, frame0,
+                                   _stream_handle(stream)), "polar_channel_awgn")
+    return llr_out
+
+
+def polar_count_errors(code: PolarCode, decoded, sent, counters, n_frames=None, stream=None):
+    """counters (CUDA int64 [2]) += (frame errors, bit errors)."""
+    n = decoded.numel() // max(code.out_row, 1) if n_frames is None else int(n_frames)
+    _check(_lib.polar_count_errors(code.handle, _dptr(decoded), _dptr(sent), n, _dptr(counters),
+                                   _stream_handle(stream)), "polar_count_errors")
+    return counters
+
+
+def polar_fer_run(code: PolarCode, is_i8: bool, ebn0_db: float, seed: int, n_frames: int,
+                  batch: int = 0):
+    """(frame errors, bit errors) of a GPU simulation of n_frames frames."""
+    fe, be = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.polar_fer_run(code.handle, int(bool(is_i8)), ebn0_db, seed, n_frames, batch,
+                              ctypes.byref(fe), ctypes.byref(be)), "polar_fer_run")
+    return fe.value, be.value
