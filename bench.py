@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-variant", action="store_true", help="skip the other LLR type")
     p.add_argument("--interpreter", action="store_true",
                    help="time the operation-list interpreter instead of the specialised decoder")
+    p.add_argument("--compile-form", choices=["auto", "full", "compact"], default="auto",
+                   help="form of the specialised decoder (auto: compact above 4096 operations)")
     p.add_argument("--mode", choices=["throughput", "mixed", "serve", "fer"], default="throughput",
                    help="throughput: one code, batch and batch-1 (default); mixed: 65,536 frames "
                         "of five codes, one persistent launch in a CUDA graph vs one launch per "
@@ -65,8 +67,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=1.0,
                    help="serve: seconds of arrivals per load (at most --serve-max-frames)")
     p.add_argument("--serve-max-frames", type=int, default=500_000)
-    p.add_argument("--serve-pool", choices=["host", "device"], default="host",
-                   help="serve: LLR pool in pinned host memory or in device memory")
+    p.add_argument("--serve-pool", default="host,device",
+                   help="serve: LLR pool in pinned host memory and/or in device memory")
     return p.parse_args()
 
 
@@ -358,7 +360,7 @@ def run_native(args, world, rank, local):
         code = polar.polar_code_create(N, K, mask)
         shape, _ = tuned_or(N, K, mask, dtype, TUNED.get((args.workload, dtype), {}))
         shape.setdefault("stage_channel", 2)
-        compile_shape(code, dtype, shape, batch, args.interpreter)
+        compile_shape(code, dtype, shape, batch, args.interpreter, args.compile_form)
         return code
 
     def throughput(dtype, steps, warmup):
@@ -437,7 +439,7 @@ def run_native(args, world, rank, local):
         i8 = main == "i8"
         lcode = polar.polar_code_create(N, K, mask)
         lshape, _ = tuned_or(N, K, mask, main, TUNED_LATENCY.get(args.workload, {}), latency=True)
-        compile_shape(lcode, main, lshape, 1, args.interpreter)
+        compile_shape(lcode, main, lshape, 1, args.interpreter, args.compile_form)
         one_in = torch.empty((1, N), dtype=r["bufs"][0].dtype, device=dev)
         one_out = torch.empty((1, row), dtype=torch.uint8, device=dev)
         h1 = torch.empty((1, row), dtype=torch.uint8).pin_memory()
@@ -487,7 +489,8 @@ def run_native(args, world, rank, local):
                    "parallelism": f"frames sharded over {world} GPU(s), no collective",
                    "l2": (f"{r['n_buf']} distinct input buffer(s) of {r['in_bytes'] / 2**20:.0f} MiB "
                           "rotated; inputs larger than L2"),
-                   "decoder": "interpreter" if args.interpreter else "specialised (NVRTC)",
+                   "decoder": "interpreter" if args.interpreter else
+                   f"specialised (NVRTC, {args.compile_form} form)",
                    "launch": r["launch"], "fer_check": r["fer"]},
         "latency_us": lat,
         "e2e": {"value": e2e_gbps, "unit": "Gbps",
@@ -563,7 +566,10 @@ def tuned_or(N, K, mask, dtype, default, latency=False):
     return {k: e[k] for k in autotune.SHAPE_KEYS if k in e}, "tuned"
 
 
-def compile_shape(code, dtype, shape, n_frames, interpreter=False):
+COMPILE_FORM = {"auto": 0, "compact": 1, "full": 2}
+
+
+def compile_shape(code, dtype, shape, n_frames, interpreter=False, form="auto"):
     """Set a launch shape (dict of polar_code_set_launch arguments, plus
     reg_subtree) and compile the specialised decoder unless timing the
     interpreter."""
@@ -573,7 +579,7 @@ def compile_shape(code, dtype, shape, n_frames, interpreter=False):
     if sh:
         polar.polar_code_set_launch(code, dtype == "i8", **sh)
     if not interpreter:
-        polar.polar_code_compile(code, dtype == "i8", n_frames, reg)
+        polar.polar_code_compile(code, dtype == "i8", n_frames, reg, COMPILE_FORM[form])
 
 
 def batch_shape(dtype):
@@ -802,19 +808,7 @@ def run_serve(args):
     budget = 4 << 30
     arms = {"served": dict(flags=0, slots=4, max_frames=4096),
             "plain": dict(flags=polar.SERVE_LAUNCH_PER_CODE, slots=1, max_frames=4096)}
-    if args.serve_pool == "device":  # LLR pool in HBM: isolates the scheduler from the host link
-        host_llr = host_llr.cuda()
-        host_out = host_out.cuda()
-    # correctness gate: one pass over the pool through each arm, bits vs transmitted
-    gate = {}
-    for name, a in arms.items():
-        host_out.zero_()
-        serve_run(polar, batch, reqs, host_llr, host_out, 2e6, P, a["flags"], a["slots"], budget,
-                  a["max_frames"], seed=1)
-        gate[name] = host_out.cpu().numpy().copy()
-    agree = bool(np.array_equal(gate["served"], gate["plain"]))
-    ferr = sum(int(not np.array_equal(gate["served"][oo[i]: oo[i] + orow[i]], want[i]))
-               for i in range(P))
+    pools = [p for p in args.serve_pool.split(",") if p]
     # host-to-device copy bandwidth from pinned memory: float32 LLRs cross this
     # link, so it bounds the coded rate the loop can take (4 bytes per coded bit)
     big = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
@@ -829,50 +823,68 @@ def run_serve(args):
     torch.cuda.synchronize()
     h2d_gbs = 3 * big.numel() * 4 / (a_.elapsed_time(b_) * 1e-3) / 1e9
     del big, dbig
-    results = []
+    results = {}
+    gates = {}
     reps = 2
     # clocks sampled once a second here: the serving loop's latency tail is what
     # is measured, and the sampler's device queries are kept rare
     with ClockSampler(0, interval_ms=1000) as clk:
-        for load in [float(x) for x in args.loads.split(",")]:
-            rate = load * 1e9 / mean_coded
-            n_total = int(min(args.serve_max_frames, max(1000, rate * args.serve_seconds)))
-            row = {"offered_coded_gbps": load, "frames": n_total, "reps": reps}
-            runs = {name: [] for name in arms}
-            for r in range(reps):  # arms interleaved, each run with its own arrivals
-                for name, a in arms.items():
-                    lat, wall, adm, launches = serve_run(polar, batch, reqs, host_llr, host_out,
-                                                         rate, n_total, a["flags"], a["slots"],
-                                                         budget, a["max_frames"],
-                                                         seed=int(load * 7) + 11 + 1000 * r)
-                    us = lat * 1e-3
-                    runs[name].append({"p50_us": float(np.percentile(us, 50)),
-                                       "p99_us": float(np.percentile(us, 99)),
-                                       "p999_us": float(np.percentile(us, 99.9)),
-                                       "info_gbps": n_total * mean_info / wall / 1e9,
-                                       "coded_gbps": n_total * mean_coded / wall / 1e9,
-                                       "admissions": adm, "launches": launches,
-                                       "frames_per_admission": n_total / max(adm, 1)})
-            for name, rs in runs.items():
-                # median over repetitions of each statistic, every repetition kept
-                row[name] = {k: float(np.median([x[k] for x in rs])) for k in rs[0]}
-                row[name]["runs"] = rs
-            results.append(row)
-            print(json.dumps({"load": row}), file=sys.stderr, flush=True)
-    top = max(results, key=lambda r: r["offered_coded_gbps"])
+        for pool in pools:
+            # pinned host memory (copies over the host link) or device memory (LLR
+            # pool in HBM: isolates the scheduler from the host link)
+            llr_buf, out_buf = (host_llr, host_out) if pool == "host" else \
+                (host_llr.cuda(), host_out.cuda())
+            # correctness gate: one pass over the pool through each arm
+            gate = {}
+            for name, a in arms.items():
+                out_buf.zero_()
+                serve_run(polar, batch, reqs, llr_buf, out_buf, 2e6, P, a["flags"], a["slots"],
+                          budget, a["max_frames"], seed=1)
+                gate[name] = out_buf.cpu().numpy().copy()
+            gates[pool] = {
+                "bits_agree": bool(np.array_equal(gate["served"], gate["plain"])),
+                "frame_errors_in_pool": sum(
+                    int(not np.array_equal(gate["served"][oo[i]: oo[i] + orow[i]], want[i]))
+                    for i in range(P))}
+            results[pool] = []
+            for load in [float(x) for x in args.loads.split(",")]:
+                rate = load * 1e9 / mean_coded
+                n_total = int(min(args.serve_max_frames, max(1000, rate * args.serve_seconds)))
+                row = {"offered_coded_gbps": load, "frames": n_total, "reps": reps}
+                runs = {name: [] for name in arms}
+                for r in range(reps):  # arms interleaved, each run with its own arrivals
+                    for name, a in arms.items():
+                        lat, wall, adm, launches = serve_run(
+                            polar, batch, reqs, llr_buf, out_buf, rate, n_total, a["flags"],
+                            a["slots"], budget, a["max_frames"], seed=int(load * 7) + 11 + 1000 * r)
+                        us = lat * 1e-3
+                        runs[name].append({"p50_us": float(np.percentile(us, 50)),
+                                           "p99_us": float(np.percentile(us, 99)),
+                                           "p999_us": float(np.percentile(us, 99.9)),
+                                           "info_gbps": n_total * mean_info / wall / 1e9,
+                                           "coded_gbps": n_total * mean_coded / wall / 1e9,
+                                           "admissions": adm, "launches": launches,
+                                           "frames_per_admission": n_total / max(adm, 1)})
+                for name, rs in runs.items():
+                    # median over repetitions of each statistic, every repetition kept
+                    row[name] = {k: float(np.median([x[k] for x in rs])) for k in rs[0]}
+                    row[name]["runs"] = rs
+                results[pool].append(row)
+                print(json.dumps({"pool": pool, "load": row}), file=sys.stderr, flush=True)
+            del llr_buf, out_buf
+    top = max(results[pools[0]], key=lambda r: r["offered_coded_gbps"])
     line = {
         "metric": "served info-bit Gbps and p50/p99 frame latency (us)", "mode": "serve",
         "value": top["served"]["info_gbps"], "unit": "Gbps", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"serve_mixed_{args.serve_pool}_pool", "codes": nk,
-                   "design_db": synth.MIXED_DESIGN_DB, "pool": args.serve_pool,
+        "config": {"workload": "serve_mixed", "codes": nk, "value_pool": pools[0],
+                   "design_db": synth.MIXED_DESIGN_DB, "pools": pools,
                    "ebn0_db": [2.0, 4.5], "arrivals": "Poisson", "pool_frames": P,
                    "device_budget_bytes": budget, "arms": arms, "batch_shape": dict(bshape, source=bsrc),
                    "latency": "completion seen by the serving thread minus scheduled arrival",
                    "h2d_pinned_gbs": h2d_gbs,
                    "h2d_bound_coded_gbps": h2d_gbs * 8 / 32},
-        "loads": results, "bits_agree": agree, "frame_errors_in_pool": ferr,
-        "clocks": clk.summary(),
+        "loads": results, "gates": gates, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 

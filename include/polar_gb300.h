@@ -215,6 +215,18 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
 polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
                                 uint32_t reg_subtree);
 
+/* polar_code_compile with a choice of form. flags = 0: the full form
+ * (every operation inlined with constant sizes) for lists of at most 4096
+ * operations, else the compact form; POLAR_COMPILE_COMPACT / _FULL force one.
+ * The compact form emits one out-of-line function per distinct register
+ * subtree (equal frozen patterns share code) and calls memory-resident
+ * operations out of line with run-time sizes, so that N = 2^20 codes (28,465
+ * operations) compile in reasonable time; results are the same bits. */
+#define POLAR_COMPILE_COMPACT 1u
+#define POLAR_COMPILE_FULL 2u
+polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frames,
+                                   uint32_t reg_subtree, uint32_t flags);
+
 /* NVRTC log of the last polar_code_compile on this handle (never NULL; valid
  * until the next compile or destroy). */
 const char *polar_code_compile_log(const polar_code_t *code);

@@ -15,6 +15,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -157,11 +158,73 @@ bool is_repspc(const std::vector<HostOp> &ops, size_t i) {
            s.off == f.off + (1u << (l - 1)) && c.kind == OP_C && c.log2n == l && c.off == f.off;
 }
 
+// The register-subtree operation i (inside a subtree entered at o0 with n0
+// leaves) as a RegSub call; returns the number of list entries it covers
+// (5 for a fused Repetition-SPC node).
+size_t emit_reg_op(std::ostream &o, const std::vector<HostOp> &ops, size_t i, uint32_t o0,
+                   const char *indent) {
+    const HostOp &op = ops[i];
+    const uint32_t n = 1u << op.log2n, p = op.off - o0;
+    if (is_repspc(ops, i)) {  // F, rep, G, spc, combine of one 8- or 16-leaf node
+        o << indent << "r.template repspc<" << n << "u, " << p << "u>();\n";
+        return 5;
+    }
+    o << indent << "r.template ";
+    switch (op.kind) {
+    case OP_F:
+    case OP_G:
+    case OP_G0R: o << "fg<" << kind_name(op.kind) << ", " << n << "u, " << p << "u>();\n"; break;
+    case OP_C: o << "combine<" << n << "u, " << p << "u, false>();\n"; break;
+    case OP_C0R: o << "combine<" << n << "u, " << p << "u, true>();\n"; break;
+    case OP_R0: o << "r0<" << n << "u, " << p << "u>();\n"; break;
+    case OP_R1: o << "r1<" << n << "u, " << p << "u>();\n"; break;
+    case OP_REP: o << "rep<" << n << "u, " << p << "u>();\n"; break;
+    default: o << "spc<" << n << "u, " << p << "u>();\n"; break;
+    }
+    return 1;
+}
+
+// Compact form: one out-of-line function per distinct register subtree (the
+// operations with offsets relative to the subtree, so equal frozen patterns
+// share code), emitted before the body; returns, per list index of a subtree's
+// first operation, the function's id.
+std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std::vector<HostOp> &ops,
+                                                const char *T, uint32_t R,
+                                                const std::string &prefix) {
+    std::map<std::string, size_t> ids;
+    std::map<size_t, size_t> at;
+    for (size_t i = 0; i < ops.size(); ++i) {
+        if (!(ops[i].flags & OPW_REG_ENTER)) continue;
+        const uint32_t o0 = ops[i].off, n0 = 1u << ops[i].log2n;
+        std::ostringstream b;
+        for (size_t j = i;;) {
+            const size_t used = emit_reg_op(b, ops, j, o0, "  ");
+            j += used;
+            if (ops[j - 1].flags & OPW_REG_EXIT) break;
+        }
+        const std::string key = std::to_string(n0) + "|" + b.str();
+        auto it = ids.find(key);
+        if (it == ids.end()) {
+            const size_t id = ids.size();
+            it = ids.emplace(key, id).first;
+            o << "__device__ __noinline__ void " << prefix << "sub" << id << "(const " << T
+              << " *in, uint32_t *beta, uint32_t o0) {\n"
+              << "  RegSub<" << T << ", " << R << "u> r;\n  r.lane = threadIdx.x & 31u;\n"
+              << "  r.template enter<" << n0 << "u>(in);\n" << b.str()
+              << "  r.template exit<" << n0 << "u>(beta, o0);\n}\n";
+        }
+        at[i] = it->second;
+    }
+    return at;
+}
+
 void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
-               uint32_t R, const std::string &name) {
+               uint32_t R, const std::string &name, bool compact = false) {
     const uint32_t N = code.N;
     const std::vector<HostOp> ops = code.build_ops(R);
     const char *T = is_i8 ? "int8_t" : "float";
+    std::map<size_t, size_t> sub_at;
+    if (compact) sub_at = emit_subtree_functions(o, ops, T, R, name + "_");
     o << "struct " << name << " {\n"
       << "  __device__ __forceinline__ void operator()(const Frame<" << T << "> &fr, float *) const {\n"
       << "    using T = " << T << ";\n"
@@ -183,6 +246,35 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     // constant arguments: out-of-line copies measured slower).
     auto mem_op = [&](const HostOp &op, const char *grp) {
         const uint32_t n = 1u << op.log2n, off = op.off;
+        if (compact) {  // out-of-line calls with run-time sizes
+            switch (op.kind) {
+            case OP_F:
+            case OP_G:
+            case OP_G0R:
+                o << "      mem_fg<T, " << grp << ", " << kind_name(op.kind) << ">(" << in(n) << ", "
+                  << out(n / 2) << ", " << n / 2 << "u, fr.beta, " << off << "u);\n";
+                break;
+            case OP_C:
+            case OP_C0R:
+                o << "      mem_combine<" << grp << ">(fr.beta, " << n << "u, " << off << "u, "
+                  << (op.kind == OP_C0R ? "true" : "false") << ");\n";
+                break;
+            case OP_R0: o << "      mem_r0<" << grp << ">(fr.beta, " << n << "u, " << off << "u);\n"; break;
+            case OP_R1:
+                o << "      mem_r1<T, " << grp << ">(" << in(n) << ", fr.beta, " << n << "u, " << off
+                  << "u);\n";
+                break;
+            case OP_REP:
+                o << "      mem_rep<T, " << grp << ">(" << in(n) << ", " << out(n / 2) << ", fr.beta, "
+                  << n << "u, " << off << "u);\n";
+                break;
+            default:
+                o << "      mem_spc<T, " << grp << ">(" << in(n) << ", fr.beta, " << n << "u, " << off
+                  << "u, fr.rkey, fr.rpar);\n";
+                break;
+            }
+            return;
+        }
         switch (op.kind) {
         case OP_F:
         case OP_G:
@@ -238,35 +330,20 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             o << "      __syncwarp();\n";
             continue;
         }
+        if (compact && (op.flags & OPW_REG_ENTER)) {  // the whole subtree is one call
+            o << "      " << name << "_sub" << sub_at.at(i) << "(" << in(n) << ", fr.beta, " << op.off
+              << "u);\n      __syncwarp();\n";
+            while (!(ops[i].flags & OPW_REG_EXIT)) ++i;
+            continue;
+        }
         if (op.flags & OPW_REG_ENTER) {
             o0 = op.off;
             n0 = n;
             o << "      {\n        RegSub<T, " << R << "u> r;\n        r.lane = lane;\n"
               << "        r.template enter<" << n0 << "u>(" << in(n0) << ");\n";
         }
-        const uint32_t p = op.off - o0;
-        if (is_repspc(ops, i)) {  // F, rep, G, spc, combine of one 8- or 16-leaf node
-            o << "        r.template repspc<" << n << "u, " << p << "u>();\n";
-            i += 4;
-            if (ops[i].flags & OPW_REG_EXIT) {
-                o << "        r.template exit<" << n0 << "u>(fr.beta, " << o0 << "u);\n      }\n"
-                  << "      __syncwarp();\n";
-            }
-            continue;
-        }
-        o << "        r.template ";
-        switch (op.kind) {
-        case OP_F:
-        case OP_G:
-        case OP_G0R: o << "fg<" << kind_name(op.kind) << ", " << n << "u, " << p << "u>();\n"; break;
-        case OP_C: o << "combine<" << n << "u, " << p << "u, false>();\n"; break;
-        case OP_C0R: o << "combine<" << n << "u, " << p << "u, true>();\n"; break;
-        case OP_R0: o << "r0<" << n << "u, " << p << "u>();\n"; break;
-        case OP_R1: o << "r1<" << n << "u, " << p << "u>();\n"; break;
-        case OP_REP: o << "rep<" << n << "u, " << p << "u>();\n"; break;
-        default: o << "spc<" << n << "u, " << p << "u>();\n"; break;
-        }
-        if (op.flags & OPW_REG_EXIT) {
+        i += emit_reg_op(o, ops, i, o0, "        ") - 1;
+        if (ops[i].flags & OPW_REG_EXIT) {
             o << "        r.template exit<" << n0 << "u>(fr.beta, " << o0 << "u);\n      }\n"
               << "      __syncwarp();\n";
         }
@@ -278,12 +355,14 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
 }  // namespace
 
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
-                            uint32_t reg_subtree) {
+                            uint32_t reg_subtree, bool compact) {
     std::ostringstream o;
-    o << "// Fast-SSC decoder specialised to one (" << code.N << ", " << code.K << ") polar code\n"
+    o << "// Fast-SSC decoder specialised to one (" << code.N << ", " << code.K << ") polar code"
+      << (compact ? " (compact form)" : "") << "\n"
       << "#include \"polar_ops.cuh\"\n"
       << "namespace polar {\n";
-    emit_body(o, code, is_i8, shape.smem_stage_max, shape.warp_stage_max, reg_subtree, "GenBody");
+    emit_body(o, code, is_i8, shape.smem_stage_max, shape.warp_stage_max, reg_subtree, "GenBody",
+              compact);
     o << "}  // namespace polar\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << shape.threads << ", "
       << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n"

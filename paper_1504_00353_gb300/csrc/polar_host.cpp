@@ -581,7 +581,15 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
 
 polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
                                 uint32_t reg_subtree) {
+    return polar_code_compile_ex(code, is_i8, n_frames, reg_subtree, 0);
+}
+
+polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frames,
+                                   uint32_t reg_subtree, uint32_t flags) {
     if (!code) return POLAR_EINVAL;
+    if (flags & ~(POLAR_COMPILE_COMPACT | POLAR_COMPILE_FULL) ||
+        (flags & POLAR_COMPILE_COMPACT && flags & POLAR_COMPILE_FULL))
+        return POLAR_EINVAL;
     if (reg_subtree == 0) reg_subtree = 256;
     if (!is_pow2(reg_subtree) || reg_subtree < 32 || reg_subtree > 1024) return POLAR_EINVAL;
     int device = -1;
@@ -622,8 +630,10 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
         gsh.ctas_per_sm = std::min(gsh.ctas_per_sm, code->user[is_i8 ? 1 : 0].ctas_per_sm);
     CompiledKernel ck;
     ck.reg_subtree = reg_subtree;
+    ck.compact = (flags & POLAR_COMPILE_COMPACT) ||
+                 (!(flags & POLAR_COMPILE_FULL) && code->ops.size() > kCompactOps);
     std::string log;
-    const std::string src = generate_source(*code, is_i8 != 0, gsh, reg_subtree);
+    const std::string src = generate_source(*code, is_i8 != 0, gsh, reg_subtree, ck.compact);
     const cudaError_t e = compile_source(src, &ck, &log);
     std::lock_guard<std::mutex> g(code->mu);
     code->compile_log = log;

@@ -20,6 +20,8 @@ namespace polar {
 
 constexpr uint32_t kMaxN = 1u << 20;
 constexpr size_t kMaxDevices = 64;
+// Operation lists longer than this are compiled in the compact form by default.
+constexpr size_t kCompactOps = 4096;
 
 struct HostOp {
     uint32_t kind, log2n, off, flags;
@@ -55,6 +57,7 @@ struct CompiledKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
     uint32_t reg_subtree = 0;
+    bool compact = false;
     std::map<int, int> occupancy;  // device -> resident CTAs per SM
     std::map<int, void *> func;    // device -> CUfunction of `kernel` in its primary context
 };
@@ -261,8 +264,11 @@ struct polar_batch {
 
 namespace polar {
 // Source text of the decoder specialised to `code` for one launch shape.
+// compact: register subtrees become one out-of-line function per distinct
+// frozen pattern and memory-resident operations out-of-line calls, so that
+// very long operation lists (N = 2^20) stay compilable.
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
-                            uint32_t reg_subtree);
+                            uint32_t reg_subtree, bool compact = false);
 // Source of the mixed-batch decoder: one specialised body per code (per-code
 // shared-memory stage cap S, warp threshold W, register subtree R).
 std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,

@@ -693,6 +693,38 @@ __device__ __forceinline__ void run_frames(const KernelArgs &a, const Body &body
     }
 }
 
+// ---------------------------------------------------------------- out-of-line forms
+
+// The memory-resident operations as real calls with run-time sizes: the compact
+// form of a generated decoder uses them so that code size grows with the number
+// of distinct subtrees, not with the length of the operation list.
+template <typename T, class Grp, uint32_t KIND>
+__device__ __noinline__ void mem_fg(const T *in, T *out, uint32_t h, const uint32_t *beta,
+                                    uint32_t o) {
+    op_fg<T, Grp, KIND>(in, out, h, beta, o);
+}
+template <class Grp>
+__device__ __noinline__ void mem_combine(uint32_t *beta, uint32_t n, uint32_t o, bool copy) {
+    op_combine<Grp>(beta, n, o, copy);
+}
+template <class Grp>
+__device__ __noinline__ void mem_r0(uint32_t *beta, uint32_t n, uint32_t o) {
+    op_r0<Grp>(beta, n, o);
+}
+template <typename T, class Grp>
+__device__ __noinline__ void mem_r1(const T *in, uint32_t *beta, uint32_t n, uint32_t o) {
+    op_r1<T, Grp>(in, beta, n, o);
+}
+template <typename T, class Grp>
+__device__ __noinline__ void mem_rep(const T *in, T *tmp, uint32_t *beta, uint32_t n, uint32_t o) {
+    op_rep<T, Grp>(in, tmp, beta, n, o);
+}
+template <typename T, class Grp>
+__device__ __noinline__ void mem_spc(const T *in, uint32_t *beta, uint32_t n, uint32_t o,
+                                     unsigned long long *rkey, uint32_t *rpar) {
+    op_spc<T, Grp>(in, beta, n, o, rkey, rpar);
+}
+
 // ---------------------------------------------------------------- mixed batches
 
 // Persistent loop of the mixed-batch kernel: each CTA claims the next frame,

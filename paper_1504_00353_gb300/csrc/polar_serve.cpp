@@ -13,9 +13,10 @@
 // batch decoder (longest codes first), copies the bits back and records an
 // event. Slots have their own stream, work counter and alpha scratch, so
 // launches admitted while others run overlap on the GPU (copies of one with
-// the decode of another, and the tail of one kernel with the next). Finished
-// slots are retired in admission order: their requests get a completion time
-// stamp and their ring space is released.
+// the decode of another, and the tail of one kernel with the next). A launch's
+// requests get their completion time stamp as soon as it is seen finished;
+// launches are retired (ring space and slot released, requests counted
+// complete) in admission order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -75,6 +76,7 @@ struct Slot {
     unsigned char *d_desc = nullptr;  // llr_off[n] | out_off[n] | code_id[n]
     unsigned char *h_desc = nullptr;  // pinned staging of the same
     uint64_t first = 0, count = 0;    // requests [first, first + count)
+    bool finished = false;            // its event completed; not yet retired
 };
 
 inline uint64_t now_ns() {
@@ -123,25 +125,38 @@ struct polar_server {
         error.compare_exchange_strong(ok, s);
     }
 
-    // Retire the oldest in-flight launch if it has finished.
+    // Stamp every in-flight launch that has finished (its requests' completion
+    // time is when it is seen finished, whatever launches are older), then
+    // retire finished launches from the oldest on: release their ring space and
+    // slot, and count their requests complete.
     bool retire() {
-        if (inflight.empty()) return false;
-        const int k = inflight.front();
-        Slot &s = slots[k];
-        const cudaError_t q = cudaEventQuery(s.done);
-        if (q == cudaErrorNotReady) return false;
-        if (q != cudaSuccess) {
-            cudaGetLastError();
-            fail(POLAR_ECUDA);
+        bool any = false;
+        for (const int k : inflight) {
+            Slot &s = slots[k];
+            if (s.finished) continue;
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                fail(POLAR_ECUDA);
+            }
+            const uint64_t t = now_ns();
+            for (uint64_t i = s.first; i < s.first + s.count; ++i) done_ns[i % capacity] = t;
+            s.finished = true;
+            any = true;
         }
-        const uint64_t t = now_ns();
-        for (uint64_t i = s.first; i < s.first + s.count; ++i) done_ns[i % capacity] = t;
-        completed.store(s.first + s.count, std::memory_order_release);
-        llr_ring.release_oldest();
-        out_ring.release_oldest();
-        inflight.pop_front();
-        free_slots.push_back(k);
-        return true;
+        while (!inflight.empty() && slots[inflight.front()].finished) {
+            const int k = inflight.front();
+            Slot &s = slots[k];
+            completed.store(s.first + s.count, std::memory_order_release);
+            llr_ring.release_oldest();
+            out_ring.release_oldest();
+            inflight.pop_front();
+            s.finished = false;
+            free_slots.push_back(k);
+            any = true;
+        }
+        return any;
     }
 
     // Admit waiting requests into one launch if a slot and ring space are free.

@@ -24,7 +24,8 @@ EXPORTS = [
     "polar_status_str", "polar_code_create", "polar_code_create_ex", "polar_code_destroy",
     "polar_code_info", "polar_code_schedule", "polar_encode_systematic", "polar_decode",
     "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
-    "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_log",
+    "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_ex",
+    "polar_code_compile_log",
     "polar_decode_noalloc", "polar_batch_create", "polar_batch_destroy", "polar_batch_decode",
     "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
     "polar_server_progress", "polar_server_destroy", "polar_random_info",
@@ -68,6 +69,7 @@ def _load():
         "polar_code_set_launch": ([vp, st, u32, u32, u32, u32, u32], st),
         "polar_code_get_launch": ([vp, st, sz, u32p, u32p, u32p, u32p, u32p, u32p, szp, szp, u32p], st),
         "polar_code_compile": ([vp, st, sz, u32], st),
+        "polar_code_compile_ex": ([vp, st, sz, u32, u32], st),
         "polar_code_compile_log": ([vp], ctypes.c_char_p),
         "polar_code_check": ([vp, vp], st),
         "polar_batch_create": ([ctypes.POINTER(vp), u32, st, u32, u32p, u32p, u32,
@@ -281,9 +283,14 @@ def polar_code_get_launch(code: PolarCode, is_i8: bool, n_frames: int) -> dict:
     return d
 
 
-def polar_code_compile(code: PolarCode, is_i8: bool, n_frames: int, reg_subtree: int = 0):
-    """Compile the decoder specialised to this code for the shape of an n_frames decode."""
-    st = _lib.polar_code_compile(code.handle, int(bool(is_i8)), n_frames, reg_subtree)
+COMPILE_COMPACT, COMPILE_FULL = 1, 2
+
+
+def polar_code_compile(code: PolarCode, is_i8: bool, n_frames: int, reg_subtree: int = 0,
+                       flags: int = 0):
+    """Compile the decoder specialised to this code for the shape of an n_frames
+    decode (flags: COMPILE_COMPACT / COMPILE_FULL to force a form)."""
+    st = _lib.polar_code_compile_ex(code.handle, int(bool(is_i8)), n_frames, reg_subtree, flags)
     if st != 0:
         raise PolarError(st, "polar_code_compile: " + polar_code_compile_log(code)[-2000:])
 

@@ -115,6 +115,44 @@ def test_repspc_heavy_masks(seed):
             assert np.array_equal(decode(c, y, i8), oracle.decode_batch(mask, y))
 
 
+@pytest.mark.parametrize("i8", [False, True])
+def test_compact_form(i8):
+    """The compact form (out-of-line subtree functions shared by equal frozen
+    patterns, out-of-line memory operations) gives the oracle's bits, for a
+    workload code at batch and batch-1 shapes and for random masks."""
+    mask, d, llr = _cases.frames(32768, 29492, 4.0, 256, seed=34, distinct=16)
+    y = synth.quantize_i8(llr) if i8 else llr
+    for n in (256, 1):
+        code = polar.polar_code_create(32768, 29492, mask)
+        polar.polar_code_compile(code, i8, n, 256, polar.COMPILE_COMPACT)
+        assert polar.polar_code_get_launch(code, i8, n)["unrolled"] == 256
+        got = decode(code, y[:n], i8)
+        assert np.array_equal(got, oracle.decode_batch(mask, y[:n]))
+    rng = np.random.default_rng(35)
+    for N in (64, 2048):
+        K = int(rng.integers(1, N))
+        m = _cases.random_mask(rng, N, K)
+        code = polar.polar_code_create(N, K, m)
+        yy = rng.integers(-127, 128, (100, N)).astype(np.int8) if i8 else \
+            (rng.standard_normal((100, N)) * 3).astype(np.float32)
+        polar.polar_code_compile(code, i8, 100, 32, polar.COMPILE_COMPACT)
+        assert np.array_equal(decode(code, yy, i8), oracle.decode_batch(m, yy))
+
+
+def test_n1m_compact_sampled():
+    """N = 2^20, K = 880,804 (28,465 operations): the default compile picks the
+    compact form; 64 int8 frames decoded, 3 compared with the oracle."""
+    N, K = 1 << 20, 880804
+    mask, d, llr = _cases.frames(N, K, 3.5, 64, seed=36, distinct=3)
+    y = synth.quantize_i8(llr)
+    code = polar.polar_code_create(N, K, mask)
+    polar.polar_code_compile(code, True, 64)
+    assert polar.polar_code_get_launch(code, True, 64)["unrolled"] == 256
+    got = decode(code, y, True)
+    sample = np.array([0, 33, 63])
+    assert np.array_equal(got[sample], oracle.decode_batch(mask, y, frames=sample))
+
+
 def test_release_returns_to_interpreter():
     mask, d, llr = _cases.frames(256, 128, 3.0, 50, seed=32)
     code = polar.polar_code_create(256, 128, mask)
