@@ -56,8 +56,10 @@ def parse():
     p.add_argument("--no-variant", action="store_true", help="skip the other LLR type")
     p.add_argument("--interpreter", action="store_true",
                    help="time the operation-list interpreter instead of the specialised decoder")
-    p.add_argument("--compile-form", choices=["auto", "full", "compact"], default="auto",
-                   help="form of the specialised decoder (auto: compact above 4096 operations)")
+    p.add_argument("--compile-form", choices=["auto", "full", "subtrees", "memory", "compact"],
+                   default="auto",
+                   help="form of the specialised decoder: what is compiled out of line (auto: "
+                        "compact above 4096 operations, else the tuned form)")
     p.add_argument("--mode", choices=["throughput", "mixed", "serve", "fer"], default="throughput",
                    help="throughput: one code, batch and batch-1 (default); mixed: 65,536 frames "
                         "of five codes, one persistent launch in a CUDA graph vs one launch per "
@@ -566,7 +568,7 @@ def tuned_or(N, K, mask, dtype, default, latency=False):
     return {k: e[k] for k in autotune.SHAPE_KEYS if k in e}, "tuned"
 
 
-COMPILE_FORM = {"auto": 0, "compact": 1, "full": 2}
+COMPILE_FORM = {"auto": 0, "subtrees": 1, "memory": 2, "compact": 3, "full": 4}
 
 
 def compile_shape(code, dtype, shape, n_frames, interpreter=False, form="auto"):

@@ -217,13 +217,16 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
 
 /* polar_code_compile with a choice of form. flags = 0: the full form
  * (every operation inlined with constant sizes) for lists of at most 4096
- * operations, else the compact form; POLAR_COMPILE_COMPACT / _FULL force one.
- * The compact form emits one out-of-line function per distinct register
- * subtree (equal frozen patterns share code) and calls memory-resident
- * operations out of line with run-time sizes, so that N = 2^20 codes (28,465
- * operations) compile in reasonable time; results are the same bits. */
-#define POLAR_COMPILE_COMPACT 1u
-#define POLAR_COMPILE_FULL 2u
+ * operations, else the compact form. POLAR_COMPILE_OUTLINE_SUBTREES emits
+ * one out-of-line function per distinct register subtree (equal frozen
+ * patterns share code); POLAR_COMPILE_OUTLINE_MEMORY calls memory-resident
+ * operations out of line with run-time sizes; POLAR_COMPILE_COMPACT is both
+ * (N = 2^20 codes, 28,465 operations, compile in about a minute);
+ * POLAR_COMPILE_FULL forces the full form. Results are the same bits. */
+#define POLAR_COMPILE_OUTLINE_SUBTREES 1u
+#define POLAR_COMPILE_OUTLINE_MEMORY 2u
+#define POLAR_COMPILE_COMPACT 3u
+#define POLAR_COMPILE_FULL 4u
 polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frames,
                                    uint32_t reg_subtree, uint32_t flags);
 

@@ -219,12 +219,13 @@ std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std
 }
 
 void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
-               uint32_t R, const std::string &name, bool compact = false) {
+               uint32_t R, const std::string &name, uint32_t outline = 0) {
+    const bool outline_sub = outline & kOutlineSubtrees, outline_mem = outline & kOutlineMemory;
     const uint32_t N = code.N;
     const std::vector<HostOp> ops = code.build_ops(R);
     const char *T = is_i8 ? "int8_t" : "float";
     std::map<size_t, size_t> sub_at;
-    if (compact) sub_at = emit_subtree_functions(o, ops, T, R, name + "_");
+    if (outline_sub) sub_at = emit_subtree_functions(o, ops, T, R, name + "_");
     o << "struct " << name << " {\n"
       << "  __device__ __forceinline__ void operator()(const Frame<" << T << "> &fr, float *) const {\n"
       << "    using T = " << T << ";\n"
@@ -246,7 +247,7 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     // constant arguments: out-of-line copies measured slower).
     auto mem_op = [&](const HostOp &op, const char *grp) {
         const uint32_t n = 1u << op.log2n, off = op.off;
-        if (compact) {  // out-of-line calls with run-time sizes
+        if (outline_mem) {  // out-of-line calls with run-time sizes
             switch (op.kind) {
             case OP_F:
             case OP_G:
@@ -330,7 +331,7 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             o << "      __syncwarp();\n";
             continue;
         }
-        if (compact && (op.flags & OPW_REG_ENTER)) {  // the whole subtree is one call
+        if (outline_sub && (op.flags & OPW_REG_ENTER)) {  // the whole subtree is one call
             o << "      " << name << "_sub" << sub_at.at(i) << "(" << in(n) << ", fr.beta, " << op.off
               << "u);\n      __syncwarp();\n";
             while (!(ops[i].flags & OPW_REG_EXIT)) ++i;
@@ -355,14 +356,15 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
 }  // namespace
 
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
-                            uint32_t reg_subtree, bool compact) {
+                            uint32_t reg_subtree, uint32_t outline) {
     std::ostringstream o;
     o << "// Fast-SSC decoder specialised to one (" << code.N << ", " << code.K << ") polar code"
-      << (compact ? " (compact form)" : "") << "\n"
+      << ((outline & kOutlineSubtrees) ? ", subtrees out of line" : "")
+      << ((outline & kOutlineMemory) ? ", memory operations out of line" : "") << "\n"
       << "#include \"polar_ops.cuh\"\n"
       << "namespace polar {\n";
     emit_body(o, code, is_i8, shape.smem_stage_max, shape.warp_stage_max, reg_subtree, "GenBody",
-              compact);
+              outline);
     o << "}  // namespace polar\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << shape.threads << ", "
       << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n"

@@ -590,6 +590,8 @@ polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frame
     if (flags & ~(POLAR_COMPILE_COMPACT | POLAR_COMPILE_FULL) ||
         (flags & POLAR_COMPILE_COMPACT && flags & POLAR_COMPILE_FULL))
         return POLAR_EINVAL;
+    uint32_t outline = flags & POLAR_COMPILE_COMPACT;  // subtrees (1) and/or memory ops (2)
+    if (!flags && code->ops.size() > kCompactOps) outline = kOutlineSubtrees | kOutlineMemory;
     if (reg_subtree == 0) reg_subtree = 256;
     if (!is_pow2(reg_subtree) || reg_subtree < 32 || reg_subtree > 1024) return POLAR_EINVAL;
     int device = -1;
@@ -630,10 +632,9 @@ polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frame
         gsh.ctas_per_sm = std::min(gsh.ctas_per_sm, code->user[is_i8 ? 1 : 0].ctas_per_sm);
     CompiledKernel ck;
     ck.reg_subtree = reg_subtree;
-    ck.compact = (flags & POLAR_COMPILE_COMPACT) ||
-                 (!(flags & POLAR_COMPILE_FULL) && code->ops.size() > kCompactOps);
+    ck.outline = outline;
     std::string log;
-    const std::string src = generate_source(*code, is_i8 != 0, gsh, reg_subtree, ck.compact);
+    const std::string src = generate_source(*code, is_i8 != 0, gsh, reg_subtree, outline);
     const cudaError_t e = compile_source(src, &ck, &log);
     std::lock_guard<std::mutex> g(code->mu);
     code->compile_log = log;

@@ -57,7 +57,7 @@ struct CompiledKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
     uint32_t reg_subtree = 0;
-    bool compact = false;
+    uint32_t outline = 0;  // kOutlineSubtrees | kOutlineMemory
     std::map<int, int> occupancy;  // device -> resident CTAs per SM
     std::map<int, void *> func;    // device -> CUfunction of `kernel` in its primary context
 };
@@ -264,11 +264,13 @@ struct polar_batch {
 
 namespace polar {
 // Source text of the decoder specialised to `code` for one launch shape.
-// compact: register subtrees become one out-of-line function per distinct
-// frozen pattern and memory-resident operations out-of-line calls, so that
-// very long operation lists (N = 2^20) stay compilable.
+// outline: kOutlineSubtrees makes every register subtree a call to one
+// out-of-line function per distinct frozen pattern; kOutlineMemory makes the
+// memory-resident operations out-of-line calls with run-time sizes. Both keep
+// very long operation lists (N = 2^20) compilable.
+constexpr uint32_t kOutlineSubtrees = 1u, kOutlineMemory = 2u;
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
-                            uint32_t reg_subtree, bool compact = false);
+                            uint32_t reg_subtree, uint32_t outline = 0);
 // Source of the mixed-batch decoder: one specialised body per code (per-code
 // shared-memory stage cap S, warp threshold W, register subtree R).
 std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,

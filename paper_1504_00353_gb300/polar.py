@@ -283,13 +283,14 @@ def polar_code_get_launch(code: PolarCode, is_i8: bool, n_frames: int) -> dict:
     return d
 
 
-COMPILE_COMPACT, COMPILE_FULL = 1, 2
+COMPILE_OUTLINE_SUBTREES, COMPILE_OUTLINE_MEMORY, COMPILE_COMPACT, COMPILE_FULL = 1, 2, 3, 4
 
 
 def polar_code_compile(code: PolarCode, is_i8: bool, n_frames: int, reg_subtree: int = 0,
                        flags: int = 0):
     """Compile the decoder specialised to this code for the shape of an n_frames
-    decode (flags: COMPILE_COMPACT / COMPILE_FULL to force a form)."""
+    decode (flags: COMPILE_OUTLINE_SUBTREES, COMPILE_OUTLINE_MEMORY, COMPILE_COMPACT,
+    COMPILE_FULL to force a form)."""
     st = _lib.polar_code_compile_ex(code.handle, int(bool(is_i8)), n_frames, reg_subtree, flags)
     if st != 0:
         raise PolarError(st, "polar_code_compile: " + polar_code_compile_log(code)[-2000:])

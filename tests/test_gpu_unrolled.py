@@ -116,15 +116,18 @@ def test_repspc_heavy_masks(seed):
 
 
 @pytest.mark.parametrize("i8", [False, True])
-def test_compact_form(i8):
-    """The compact form (out-of-line subtree functions shared by equal frozen
-    patterns, out-of-line memory operations) gives the oracle's bits, for a
+@pytest.mark.parametrize("form", ["compact", "subtrees", "memory"])
+def test_outlined_forms(i8, form):
+    """Out-of-line forms (subtree functions shared by equal frozen patterns,
+    out-of-line memory operations, or both) give the oracle's bits, for a
     workload code at batch and batch-1 shapes and for random masks."""
+    flags = {"compact": polar.COMPILE_COMPACT, "subtrees": polar.COMPILE_OUTLINE_SUBTREES,
+             "memory": polar.COMPILE_OUTLINE_MEMORY}[form]
     mask, d, llr = _cases.frames(32768, 29492, 4.0, 256, seed=34, distinct=16)
     y = synth.quantize_i8(llr) if i8 else llr
     for n in (256, 1):
         code = polar.polar_code_create(32768, 29492, mask)
-        polar.polar_code_compile(code, i8, n, 256, polar.COMPILE_COMPACT)
+        polar.polar_code_compile(code, i8, n, 256, flags)
         assert polar.polar_code_get_launch(code, i8, n)["unrolled"] == 256
         got = decode(code, y[:n], i8)
         assert np.array_equal(got, oracle.decode_batch(mask, y[:n]))
@@ -135,7 +138,7 @@ def test_compact_form(i8):
         code = polar.polar_code_create(N, K, m)
         yy = rng.integers(-127, 128, (100, N)).astype(np.int8) if i8 else \
             (rng.standard_normal((100, N)) * 3).astype(np.float32)
-        polar.polar_code_compile(code, i8, 100, 32, polar.COMPILE_COMPACT)
+        polar.polar_code_compile(code, i8, 100, 32, flags)
         assert np.array_equal(decode(code, yy, i8), oracle.decode_batch(m, yy))
 
 
