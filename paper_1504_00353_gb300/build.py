@@ -21,6 +21,7 @@ SOURCES = [os.path.join(CSRC, "polar_host.cpp"), os.path.join(CSRC, "polar_codeg
            os.path.join(CSRC, "polar_kernels.cu"), os.path.join(CSRC, "polar_chain.cu")]
 GEN = os.path.join(HERE, "_build")  # generated include: polar_ops.cuh as a C++ string
 HEADERS = [os.path.join(CSRC, "polar_internal.h"), os.path.join(CSRC, "polar_ops.cuh"),
+           os.path.join(CSRC, "polar_ring.h"),
            os.path.join(ROOT, "include", "polar_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

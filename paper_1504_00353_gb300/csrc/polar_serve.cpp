@@ -30,43 +30,11 @@
 
 #include "polar_gb300.h"
 #include "polar_internal.h"
+#include "polar_ring.h"
 
 using namespace polar;
 
 namespace {
-
-// First-in first-out allocator of contiguous byte ranges in a ring of `cap`
-// bytes: ranges are released in the order they were taken.
-struct Ring {
-    struct Range {
-        size_t lo, hi;
-    };
-    size_t cap = 0, head = 0;
-    std::deque<Range> live;
-
-    // Largest range alloc() can return now.
-    size_t avail() const {
-        if (live.empty()) return cap;
-        const size_t tail = live.front().lo;
-        if (head > tail) return std::max(cap - head, tail);  // [head, cap) or wrap to [0, tail)
-        return tail - head;                                   // wrapped: [head, tail)
-    }
-    // Take b bytes (0 < b <= avail()).
-    Range alloc(size_t b) {
-        size_t lo = 0;
-        if (!live.empty()) {
-            const size_t tail = live.front().lo;
-            lo = (head > tail && cap - head < b) ? 0 : head;
-        }
-        head = lo + b;
-        live.push_back({lo, lo + b});
-        return live.back();
-    }
-    void release_oldest() {
-        live.pop_front();
-        if (live.empty()) head = 0;
-    }
-};
 
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -104,7 +72,7 @@ struct polar_server {
 
     unsigned char *d_llr = nullptr;
     uint8_t *d_out = nullptr;
-    Ring llr_ring, out_ring;
+    polar::Ring llr_ring, out_ring;
     std::vector<Slot> slots;
     std::vector<int> free_slots;
     std::deque<int> inflight;
@@ -178,7 +146,7 @@ struct polar_server {
         Slot &s = slots[k];
         s.first = admitted;
         s.count = n;
-        const Ring::Range rl = llr_ring.alloc(bl), ro = out_ring.alloc(bo);
+        const polar::Ring::Range rl = llr_ring.alloc(bl), ro = out_ring.alloc(bo);
 
         // descriptors, longest codes first (stable: arrival order among equals)
         order.resize(n);
