@@ -158,6 +158,17 @@ polar_status polar_decode_noalloc(const polar_code_t *code, const float *llr,
  * every F, G and G_0R operation). */
 size_t polar_code_trace_len(const polar_code_t *code);
 
+/* Decode frames held in host memory: n_frames frames of N LLRs (float32
+ * with is_i8 = 0, int8 in [-127, 127] with is_i8 = 1) at host_llr, packed
+ * information bits to host_bits ([n][ceil(K/8)] bytes). The frames are cut
+ * into chunks of chunk_frames (0 = n_frames / 8) that move through three
+ * internal streams, so copies in and out overlap decoding; the paper's latency
+ * likewise counts the copies into and out of decoder memory (Sec. III). Pinned
+ * host memory (cudaMallocHost) is needed for the overlap. Blocking: returns
+ * when host_bits is complete; POLAR_ETIMEOUT as polar_code_check. */
+polar_status polar_decode_host(const polar_code_t *code, int is_i8, const void *host_llr,
+                               uint8_t *host_bits, size_t n_frames, size_t chunk_frames);
+
 /* Test/debug decode that also records, for every frame and in list order, the
  * N_v/2 output LLRs of each F, G and G_0R operation into
  *   alpha_trace  device, [n_frames][polar_code_trace_len()] float32

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpolar_gb300.so")
 SOURCES = [os.path.join(CSRC, "polar_host.cpp"), os.path.join(CSRC, "polar_codegen.cpp"),
            os.path.join(CSRC, "polar_batch.cpp"), os.path.join(CSRC, "polar_serve.cpp"),
-           os.path.join(CSRC, "polar_kernels.cu"), os.path.join(CSRC, "polar_chain.cu")]
+           os.path.join(CSRC, "polar_kernels.cu"), os.path.join(CSRC, "polar_chain.cu"),
+           os.path.join(CSRC, "polar_hostio.cpp")]
 GEN = os.path.join(HERE, "_build")  # generated include: polar_ops.cuh as a C++ string
 HEADERS = [os.path.join(CSRC, "polar_internal.h"), os.path.join(CSRC, "polar_ops.cuh"),
            os.path.join(CSRC, "polar_ring.h"),

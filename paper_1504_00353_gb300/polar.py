@@ -30,6 +30,7 @@ EXPORTS = [
     "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
     "polar_server_progress", "polar_server_destroy", "polar_random_info",
     "polar_encode_systematic_device", "polar_channel_awgn", "polar_count_errors", "polar_fer_run",
+    "polar_decode_host",
 ]
 
 # struct polar_request
@@ -86,6 +87,7 @@ def _load():
                                    ctypes.POINTER(ctypes.c_uint64)], st),
         "polar_server_destroy": ([vp], st),
         "polar_random_info": ([vp, vp, sz, ctypes.c_uint64, ctypes.c_uint64, vp], st),
+        "polar_decode_host": ([vp, st, vp, vp, sz, sz], st),
         "polar_encode_systematic_device": ([vp, vp, vp, sz, vp], st),
         "polar_channel_awgn": ([vp, vp, vp, st, sz, ctypes.c_float, ctypes.c_uint64,
                                 ctypes.c_uint64, vp], st),
@@ -241,6 +243,27 @@ def polar_decode_i8(code: PolarCode, llr, bits_out=None, n_frames=None, stream=N
     import torch
     return _decode(_lib.polar_decode_i8, "polar_decode_i8", code, llr, bits_out, n_frames,
                    stream, torch.int8)
+
+
+def polar_decode_host(code: PolarCode, llr, bits_out=None, chunk_frames: int = 0):
+    """Decode LLRs held in host memory (a CPU tensor, pinned for overlap, or a
+    numpy array; float32 or int8 [n, N]) into host bits [n, ceil(K/8)]; copies
+    overlap decoding through chunked internal streams. Blocking."""
+    import torch
+    if isinstance(llr, np.ndarray):
+        llr = torch.from_numpy(np.ascontiguousarray(llr))
+    if llr.is_cuda or not llr.is_contiguous() or llr.dtype not in (torch.float32, torch.int8):
+        raise TypeError("llr must be a contiguous host float32 or int8 tensor")
+    n = llr.numel() // code.N
+    if bits_out is None:
+        bits_out = torch.empty((n, code.out_row), dtype=torch.uint8)
+    if bits_out.is_cuda or bits_out.dtype != torch.uint8 or bits_out.numel() < n * code.out_row:
+        raise ValueError("bits_out must be a host uint8 tensor of n*ceil(K/8) bytes")
+    _check(_lib.polar_decode_host(code.handle, 1 if llr.dtype == torch.int8 else 0,
+                                  ctypes.c_void_p(llr.data_ptr()),
+                                  ctypes.c_void_p(bits_out.data_ptr()), n, chunk_frames),
+           "polar_decode_host")
+    return bits_out
 
 
 def polar_decode_trace(code: PolarCode, llr, bits_out=None, trace=None, stream=None):

@@ -164,3 +164,19 @@ def test_release_returns_to_interpreter():
     polar.polar_code_compile(code, False, 0)
     assert polar.polar_code_get_launch(code, False, 50)["unrolled"] == 0
     assert np.array_equal(decode(code, llr, False), oracle.decode_batch(mask, llr))
+
+
+@pytest.mark.parametrize("i8", [False, True])
+def test_decode_from_host_buffers(i8):
+    """polar_decode_host (chunked copies overlapped with decoding) gives the
+    oracle's bits, with chunk sizes that leave a ragged last chunk."""
+    mask, d, llr = _cases.frames(1024, 512, 2.5, 1000, seed=37, distinct=100)
+    y = synth.quantize_i8(llr) if i8 else llr
+    code = polar.polar_code_create(1024, 512, mask)
+    want = oracle.decode_batch(mask, y)
+    host = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
+    for chunk in (0, 1, 128, 333, 1000, 5000):
+        got = polar.polar_decode_host(code, host, chunk_frames=chunk)
+        assert np.array_equal(got.numpy(), want), chunk
+    got = polar.polar_decode_host(code, y)  # pageable numpy input also works
+    assert np.array_equal(got.numpy(), want)
