@@ -409,7 +409,7 @@ def run_native(args, world, rank, local):
     e2e_gbps, e2e_chunk = None, None
     if not args.no_e2e:
         e2e_steps = max(3, args.steps // 2)
-        for chunk in sorted({max(1, batch // 4), max(1, batch // 8), max(1, batch // 16)}):
+        for chunk in sorted({max(1, batch // 2), max(1, batch // 4), max(1, batch // 8)}):
             for _ in range(2):
                 polar.polar_decode_host(code, host_in, host_out, chunk)
             barrier(world)

@@ -270,7 +270,7 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     void *scratch = nullptr;
     const size_t scratch_bytes = size_t(sh.grid) * sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
     if (scratch_bytes) {
-        cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, s);
+        cudaError_t e = pool_alloc(&scratch, scratch_bytes, device, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return cuda_status(e);
@@ -296,6 +296,35 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
 namespace polar {
 polar_status code_device_state(polar_code *c, int device, DeviceState **out) {
     return ensure_device(c, device, out);
+}
+
+cudaMemPool_t device_pool(int device) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools(kMaxDevices, nullptr);
+    static std::vector<bool> tried(kMaxDevices, false);
+    if (device < 0 || static_cast<size_t>(device) >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!tried[device]) {
+        tried[device] = true;
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) == cudaSuccess) {
+            uint64_t keep = ~0ull;  // never hand cached blocks back to the driver
+            cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[device] = p;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return pools[device];
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, int device, cudaStream_t s) {
+    cudaMemPool_t pool = device_pool(device);
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
 }
 }  // namespace polar
 

@@ -3,7 +3,7 @@
 // cut into chunks; chunk c goes to one of kDepth internal streams (copy in,
 // decode, copy out), so while one chunk decodes the next is copied in and the
 // previous one copied out. Device buffers for the chunks in flight come from
-// the stream-ordered allocator and are returned at the end of the call.
+// the library's stream-ordered pool (cached between calls).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,10 +71,10 @@ polar_status polar_decode_host(const polar_code_t *code, int is_i8, const void *
     uint8_t *d_out[kDepth] = {};
     polar_status st = POLAR_OK;
     for (int k = 0; k < depth && st == POLAR_OK; ++k) {
-        st = status_of(cudaMallocAsync(&d_in[k], chunk_frames * in_row, hs.s[k]));
+        st = status_of(polar::pool_alloc(&d_in[k], chunk_frames * in_row, device, hs.s[k]));
         if (st == POLAR_OK && out_row)
-            st = status_of(cudaMallocAsync(reinterpret_cast<void **>(&d_out[k]),
-                                           chunk_frames * out_row, hs.s[k]));
+            st = status_of(polar::pool_alloc(reinterpret_cast<void **>(&d_out[k]),
+                                             chunk_frames * out_row, device, hs.s[k]));
     }
     const unsigned char *src = static_cast<const unsigned char *>(host_llr);
     for (size_t c = 0; c < n_chunks && st == POLAR_OK; ++c) {

@@ -288,6 +288,13 @@ int compiled_max_ctas(CompiledKernel *ck, uint32_t threads, size_t smem_bytes);
 // Launch a compiled decoder on the current device.
 cudaError_t launch_compiled(CompiledKernel *ck, const LaunchShape &shape, const void *args,
                             cudaStream_t stream);
+// The library's stream-ordered memory pool on `device` (created on first use):
+// freed blocks stay cached in it, so per-call scratch does not go back to the
+// driver at every synchronisation (the default pool releases at a threshold of
+// zero). Returns nullptr if the pool cannot be created.
+cudaMemPool_t device_pool(int device);
+// cudaMallocAsync from that pool (falls back to the default pool).
+cudaError_t pool_alloc(void **p, size_t bytes, int device, cudaStream_t s);
 // The code's tables on `device` (uploaded on first use): op words, trace
 // offsets and the info-bit packing tables (see DeviceState).
 polar_status code_device_state(polar_code *c, int device, DeviceState **out);
