@@ -288,6 +288,7 @@ void polar_batch_destroy(polar_batch_t *batch);
  *   llr_off[i]  element offset of frame i's N LLRs in `llr` (16-byte aligned
  *               frame start: a multiple of 4 for float32, 16 for int8);
  *   out_off[i]  byte offset of frame i's ceil(K/8) output bytes in bits_out.
+ * n_frames is at most 2^32 - 1 (POLAR_EINVAL above: the work counter is 32-bit).
  * Frames are claimed in index order, so listing the longest codes first gives
  * the best balance. The grid is min(resident CTAs, n_frames). Calls on one
  * batch decoder share its work counter and scratch: they must not overlap on

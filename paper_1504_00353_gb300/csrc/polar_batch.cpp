@@ -192,6 +192,7 @@ polar_status polar_batch_decode(polar_batch_t *b, const uint32_t *code_id, const
     if (!b) return POLAR_EINVAL;
     if (n_frames == 0) return POLAR_OK;
     if (!code_id || !llr_off || !out_off || !llr || !bits_out) return POLAR_EINVAL;
+    if (n_frames > 0xFFFFFFFFull) return POLAR_EINVAL;  // the work counter is 32-bit
     if (reinterpret_cast<uintptr_t>(llr) % 16 != 0) return POLAR_EALIGN;
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess || device != b->device) {

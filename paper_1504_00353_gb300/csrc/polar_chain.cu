@@ -270,8 +270,20 @@ polar_status polar_encode_systematic_device(const polar_code_t *code, const uint
     if (st != POLAR_OK) return st;
     const size_t nops = c->ops.size();
     const uint32_t nw = c->N >= 32 ? c->N / 32 : 1;
+    const size_t smem = nw * sizeof(uint32_t);  // the frame's N bits: 128 KB at N = 2^20
+    if (smem > 48 * 1024) {
+        static std::mutex mu;
+        static size_t raised[64] = {};
+        std::lock_guard<std::mutex> g(mu);
+        if (device < 64 && raised[device] < smem) {
+            const cudaError_t e = cudaFuncSetAttribute(
+                encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            if (e != cudaSuccess) return status_of(e);
+            raised[device] = smem;
+        }
+    }
     const int grid = static_cast<int>(std::min<size_t>(n_frames, 152 * 8));
-    encode_kernel<<<grid, 256, nw * sizeof(uint32_t), reinterpret_cast<cudaStream_t>(stream)>>>(
+    encode_kernel<<<grid, 256, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
         info_packed, codeword_packed, ds->tables + 2 * nops, ds->tables + 2 * nops + c->NW, c->N,
         c->K, n_frames);
     return status_of(cudaGetLastError());

@@ -135,3 +135,11 @@ def test_mixed_full_size_sampled():
     for i, w in want.items():
         assert np.array_equal(got[oo[i]: oo[i] + orow[i]], w), i
     assert (got != 0xA5).any()
+
+
+def test_batch_rejects_oversized_frame_count():
+    codes = [polar.polar_code_create(N, K, synth.frozen_mask(N, K, 3.0)) for N, K in CODES[:2]]
+    batch = polar.polar_batch_create(codes, True, 32)
+    z = torch.zeros(16, dtype=torch.int64, device="cuda")
+    with pytest.raises(polar.PolarError):
+        polar.polar_batch_decode(batch, z, z, z, z, z.to(torch.uint8), n_frames=1 << 32)

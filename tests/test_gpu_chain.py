@@ -37,18 +37,19 @@ def test_random_info_is_philox(K):
         assert np.array_equal(got[f], _philox.info_bytes(K, seed, frame0 + f)), f
 
 
-@pytest.mark.parametrize("N,K,db", [(8, 4, 2.0), (16, 11, 3.0), (1024, 512, 2.5), (2048, 1723, 3.0),
-                                    (32768, 29492, 4.0)])
-def test_device_encoder_matches_oracle(N, K, db):
+@pytest.mark.parametrize("N,K,db,n", [(8, 4, 2.0, 40), (16, 11, 3.0, 40), (1024, 512, 2.5, 40),
+                                      (2048, 1723, 3.0, 40), (32768, 29492, 4.0, 40),
+                                      (1 << 20, 880804, 3.5, 2)])
+def test_device_encoder_matches_oracle(N, K, db, n):
     mask = synth.frozen_mask(N, K, db)
     code = polar.polar_code_create(N, K, mask)
     rng = np.random.default_rng(N)
-    d = synth.info_bits(rng, 40, K)
+    d = synth.info_bits(rng, n, K)
     info = torch.from_numpy(synth.pack_bits(d)).cuda()
-    cw = cuda_u8((40, (N + 7) // 8))
+    cw = cuda_u8((n, (N + 7) // 8))
     polar.polar_encode_systematic_device(code, info, cw)
     got = synth.unpack_bits(cw.cpu().numpy(), N)
-    for f in range(40):
+    for f in range(n):
         assert np.array_equal(got[f], oracle.encode_systematic(mask, d[f])), f
 
 
