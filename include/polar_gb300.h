@@ -421,6 +421,15 @@ polar_status polar_fer_run(const polar_code_t *code, int is_i8, float ebn0_db, u
                            size_t n_frames, size_t batch, uint64_t *frame_errors,
                            uint64_t *bit_errors);
 
+/* Self-test of the device-side failure path (the paper has no counterpart):
+ * launches one CTA whose mbarrier wait is never completed; the wait gives up
+ * after limit_us microseconds (1..1,000,000), as the channel-staging wait does
+ * after 2 s, and sets the handle's status word, so that the next
+ * polar_code_check returns POLAR_ETIMEOUT. Nothing faults and nothing hangs;
+ * the context stays usable. Asynchronous on `stream`. */
+polar_status polar_selftest_bounded_wait(polar_code_t *code, uint32_t limit_us,
+                                         polar_stream_t stream);
+
 /* Wait for `stream`, then read and clear the handle's device status word on
  * the current device. POLAR_ETIMEOUT if a bounded device wait expired since
  * the last check, POLAR_OK otherwise. */

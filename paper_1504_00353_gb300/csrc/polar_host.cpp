@@ -679,6 +679,21 @@ const char *polar_code_compile_log(const polar_code_t *code) {
     return code ? code->compile_log.c_str() : "";
 }
 
+polar_status polar_selftest_bounded_wait(polar_code_t *code, uint32_t limit_us,
+                                         polar_stream_t stream) {
+    if (!code || limit_us == 0 || limit_us > 1000000) return POLAR_EINVAL;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    DeviceState *ds = nullptr;
+    const polar_status st = ensure_device(code, device, &ds);
+    if (st != POLAR_OK) return st;
+    return cuda_status(launch_bounded_wait_selftest(
+        ds->status, 1000ull * limit_us, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 polar_status polar_code_check(polar_code_t *code, polar_stream_t stream) {
     if (!code) return POLAR_EINVAL;
     int device = -1;

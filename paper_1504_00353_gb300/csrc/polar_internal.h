@@ -89,6 +89,11 @@ constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 // device looks it up with cudaGetSymbolAddress (no allocation).
 cudaError_t noalloc_scratch(void **ptr);
 
+// Launch the bounded-wait self-test: a wait that nothing completes gives up
+// after limit_ns and sets bit 0 of *status (device memory).
+cudaError_t launch_bounded_wait_selftest(int *status, unsigned long long limit_ns,
+                                         cudaStream_t stream);
+
 // Launch the interpreter kernel. Returns the CUDA error of the launch.
 cudaError_t launch_decode(bool is_i8, bool trace, bool stage_channel,
                           const LaunchShape &shape, const KernelArgs &args,

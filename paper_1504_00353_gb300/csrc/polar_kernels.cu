@@ -322,6 +322,25 @@ int kernel_max_ctas_per_sm(bool is_i8, bool stage, uint32_t threads, size_t smem
     return n;
 }
 
+// Self-test of the bounded wait: an mbarrier that expects one arrival which
+// never comes; the wait gives up after limit_ns, exactly as the channel-staging
+// wait does, and reports through the status word. No copy is in flight, so the
+// CTA can leave at once.
+__global__ void bounded_wait_selftest_kernel(int *status, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(&bar, 0u, limit_ns)) atomicOr(status, 1);
+    }
+}
+
+cudaError_t launch_bounded_wait_selftest(int *status, unsigned long long limit_ns,
+                                         cudaStream_t stream) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(status, limit_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decode(bool is_i8, bool trace, bool stage, const LaunchShape &shape,
                           const KernelArgs &args, cudaStream_t stream) {
     const void *k = select_kernel(is_i8, trace, stage);

@@ -580,8 +580,10 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait for the phase with the given parity; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false after limit_ns (or
+// kWaitPolls polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
     const unsigned long long t0 = globaltimer();
     for (uint32_t i = 0; i < kWaitPolls; ++i) {
         uint32_t ok;
@@ -590,7 +592,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
         if (ok) return true;
-        if ((i & 63u) == 63u && globaltimer() - t0 > kWaitNs) return false;
+        if ((i & 63u) == 63u && globaltimer() - t0 > limit_ns) return false;
     }
     return false;
 }

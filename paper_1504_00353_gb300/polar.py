@@ -30,7 +30,7 @@ EXPORTS = [
     "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
     "polar_server_progress", "polar_server_destroy", "polar_random_info",
     "polar_encode_systematic_device", "polar_channel_awgn", "polar_count_errors", "polar_fer_run",
-    "polar_decode_host",
+    "polar_decode_host", "polar_selftest_bounded_wait",
 ]
 
 # struct polar_request
@@ -88,6 +88,7 @@ def _load():
         "polar_server_destroy": ([vp], st),
         "polar_random_info": ([vp, vp, sz, ctypes.c_uint64, ctypes.c_uint64, vp], st),
         "polar_decode_host": ([vp, st, vp, vp, sz, sz], st),
+        "polar_selftest_bounded_wait": ([vp, u32, vp], st),
         "polar_encode_systematic_device": ([vp, vp, vp, sz, vp], st),
         "polar_channel_awgn": ([vp, vp, vp, st, sz, ctypes.c_float, ctypes.c_uint64,
                                 ctypes.c_uint64, vp], st),
@@ -325,6 +326,13 @@ def polar_code_compile_log(code: PolarCode) -> str:
 
 def polar_code_check(code: PolarCode, stream=None):
     _check(_lib.polar_code_check(code.handle, _stream_handle(stream)), "polar_code_check")
+
+
+def polar_selftest_bounded_wait(code: PolarCode, limit_us: int, stream=None):
+    """Launch a device wait that nothing completes; it gives up after limit_us and
+    marks the handle, so the next polar_code_check raises POLAR_ETIMEOUT."""
+    _check(_lib.polar_selftest_bounded_wait(code.handle, limit_us, _stream_handle(stream)),
+           "polar_selftest_bounded_wait")
 
 
 def polar_status_str(status: int) -> str:

@@ -231,3 +231,24 @@ def test_get_launch_reports_shape():
             sh = polar.polar_code_get_launch(code, i8, n)
             assert sh["grid"] >= 1 and sh["threads"] % 32 == 0
             assert sh["smem_bytes"] <= 232448
+
+
+# ---------------------------------------------------------------- failure path
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A device wait that nothing completes gives up after its limit and reports
+    POLAR_ETIMEOUT through polar_code_check (once: the word is cleared); decoding
+    on the same context still gives the oracle's bits afterwards."""
+    import time
+    mask, d, llr = _cases.frames(1024, 512, 2.5, 8, seed=38)
+    code = polar.polar_code_create(1024, 512, mask)
+    t0 = time.monotonic()
+    polar.polar_selftest_bounded_wait(code, 2000)  # 2 ms
+    with pytest.raises(polar.PolarError) as e:
+        polar.polar_code_check(code)
+    assert e.value.status == -5  # POLAR_ETIMEOUT
+    assert time.monotonic() - t0 < 10
+    polar.polar_code_check(code)  # cleared
+    assert np.array_equal(gpu_decode(code, llr, False), oracle_bits(mask, llr))
+    with pytest.raises(polar.PolarError):
+        polar.polar_selftest_bounded_wait(code, 0)
