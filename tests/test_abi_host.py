@@ -122,3 +122,19 @@ def test_create_rejects_bad_arguments(N, K, mask):
 def test_status_strings():
     for s in (0, -1, -2, -3, -4, -5):
         assert polar.polar_status_str(s)
+
+
+def test_public_header_is_plain_c(tmp_path):
+    """include/polar_gb300.h is a C header: it compiles as strict C99 with no
+    warnings (no C++ or torch types in the boundary)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "polar_gb300.h"\nint main(void) { return 0; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
