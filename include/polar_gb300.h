@@ -116,8 +116,12 @@ polar_status polar_encode_systematic(const polar_code_t *code, const uint8_t *in
  * Arithmetic: F is an exact min and sign, G one IEEE binary32 add, the
  * Repetition sum folds t[i] + t[i+m] for m = N_v/2, ..., 1 (the order SC
  * uses), SPC flips the lowest index of least |LLR|; results are bit-exact
- * with a scalar CPU evaluation in that order. Device scratch, when the code
- * needs it, is taken with cudaMallocAsync on `stream` and returned on it.
+ * with a scalar CPU evaluation in that order. The decoder specialised to this
+ * code runs when polar_code_compile built one for the decode's launch shape,
+ * the operation-list interpreter otherwise; both give the same bits. Device
+ * scratch, when the code needs it, is taken on `stream` from the library's
+ * stream-ordered memory pool (freed blocks stay cached in it for later calls)
+ * and returned on it.
  * Returns POLAR_EALIGN for a misaligned llr, POLAR_EINVAL for NULL pointers,
  * POLAR_ECUDA when no device is present or the launch fails. */
 polar_status polar_decode(const polar_code_t *code, const float *llr, uint8_t *bits_out,
