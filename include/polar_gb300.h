@@ -165,7 +165,7 @@ size_t polar_code_trace_len(const polar_code_t *code);
 /* Decode frames held in host memory: n_frames frames of N LLRs (float32
  * with is_i8 = 0, int8 in [-127, 127] with is_i8 = 1) at host_llr, packed
  * information bits to host_bits ([n][ceil(K/8)] bytes). The frames are cut
- * into chunks of chunk_frames (0 = n_frames / 8) that move through three
+ * into chunks of chunk_frames (0 = n_frames / 8) that move through six
  * internal streams, so copies in and out overlap decoding; the paper's latency
  * likewise counts the copies into and out of decoder memory (Sec. III). Pinned
  * host memory (cudaMallocHost) is needed for the overlap. Blocking: returns

@@ -15,7 +15,7 @@
 
 namespace {
 
-constexpr int kDepth = 3;
+constexpr int kDepth = 6;  // chunks in flight: buffers are reused only beyond this
 
 struct HostIoStreams {
     cudaStream_t s[kDepth] = {};
