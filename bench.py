@@ -571,8 +571,10 @@ def compile_shape(code, dtype, shape, n_frames, interpreter=False, form="auto"):
     from paper_1504_00353_gb300 import polar
     sh = dict(shape)
     reg = sh.pop("reg_subtree", 0)
+    fpc = sh.pop("frames_per_cta", 1)
     if sh:
         polar.polar_code_set_launch(code, dtype == "i8", **sh)
+    polar.polar_code_set_frames_per_cta(code, dtype == "i8", fpc)
     if not interpreter:
         polar.polar_code_compile(code, dtype == "i8", n_frames, reg, COMPILE_FORM[form])
 

@@ -201,9 +201,25 @@ polar_status polar_code_set_launch(polar_code_t *code, int is_i8, uint32_t threa
                                    uint32_t smem_stage_max, uint32_t warp_stage_max,
                                    uint32_t ctas_per_sm, uint32_t stage_channel);
 
+/* Several frames per CTA, one per warp (frames = 2, 4 or 8; 0 or 1 = one
+ * frame per CTA), for throughput shapes of one warp per frame (threads = 32):
+ * the CTA's warps decode different frames side by side with the same
+ * straight-line decoder, kept in step by CTA barriers so that they share the
+ * instructions they fetch. Applies to the specialised decoder only: compile
+ * after setting it (polar_code_compile); decodes whose shape has no such
+ * decoder, batch-1 shapes and the interpreter keep one frame per CTA.
+ * Not thread-safe against concurrent decodes of the same handle. */
+polar_status polar_code_set_frames_per_cta(polar_code_t *code, int is_i8, uint32_t frames);
+
+/* Frames per CTA a decode of n_frames frames would run with now (1 when the
+ * several-frames form does not apply or has not been compiled). */
+polar_status polar_code_get_frames_per_cta(const polar_code_t *code, int is_i8, size_t n_frames,
+                                           uint32_t *frames);
+
 /* The launch shape a decode of n_frames frames would use now (after the
- * automatic choices), written to the non-NULL pointers. smem_bytes is the
- * dynamic shared memory per CTA, grid the number of CTAs, scratch_bytes the
+ * automatic choices), written to the non-NULL pointers. threads is per CTA
+ * (32 x frames per CTA in the several-frames form), smem_bytes the dynamic
+ * shared memory per CTA, grid the number of CTAs, scratch_bytes the
  * device scratch the call allocates, unrolled the register-subtree size of the
  * specialised decoder that will run (0: the operation-list interpreter). */
 polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n_frames,

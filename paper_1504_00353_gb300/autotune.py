@@ -103,8 +103,8 @@ def frames_for(N: int, sms: int) -> int:
 
 
 SHAPE_KEYS = ("threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm", "stage_channel",
-              "reg_subtree")
-SHAPE_DEFAULTS = dict(ctas_per_sm=0, stage_channel=2, reg_subtree=256)
+              "reg_subtree", "frames_per_cta")
+SHAPE_DEFAULTS = dict(ctas_per_sm=0, stage_channel=2, reg_subtree=256, frames_per_cta=1)
 
 
 def _shape_key(s: dict) -> tuple:
@@ -122,6 +122,7 @@ def apply_shape(code, dtype: str, shape: dict, n_frames: int):
                                 smem_stage_max=sh["smem_stage_max"],
                                 warp_stage_max=sh["warp_stage_max"],
                                 ctas_per_sm=sh["ctas_per_sm"], stage_channel=sh["stage_channel"])
+    polar.polar_code_set_frames_per_cta(code, dtype == "i8", sh["frames_per_cta"])
     polar.polar_code_compile(code, dtype == "i8", n_frames, sh["reg_subtree"])
 
 
@@ -271,6 +272,11 @@ class CodeTuner:
         if tune_ctas:  # fewer resident frames per SM, more registers per thread
             top = min(32, 2048 // T)
             self.measure([dict(cur, ctas_per_sm=c) for c in (8, 12, 16, 20, 24, 28) if c < top])
+            cur, _ = self.best(T)
+            if T == 32:  # several frames per CTA, one per warp (ctas_per_sm counts CTAs)
+                self.measure([dict(cur, frames_per_cta=f,
+                                   ctas_per_sm=(cur["ctas_per_sm"] + f - 1) // f if cur["ctas_per_sm"] else 0)
+                              for f in (2, 4)])
         return self.best(T)
 
 

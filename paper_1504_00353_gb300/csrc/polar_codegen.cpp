@@ -218,8 +218,12 @@ std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std
     return at;
 }
 
+// warp_frames: the body for several frames per CTA, one per warp (run by
+// run_warp_frames): every operation is warp-level on the warp's own frame, and
+// a CTA barrier after each register subtree keeps the warps in step.
 void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
-               uint32_t R, const std::string &name, uint32_t outline = 0) {
+               uint32_t R, const std::string &name, uint32_t outline = 0,
+               bool warp_frames = false) {
     const bool outline_sub = outline & kOutlineSubtrees, outline_mem = outline & kOutlineMemory;
     const uint32_t N = code.N;
     const std::vector<HostOp> ops = code.build_ops(R);
@@ -311,7 +315,7 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     for (size_t i = 0; i < ops.size(); ++i) {
         const HostOp &op = ops[i];
         const uint32_t n = 1u << op.log2n;
-        const bool narrow = n <= W || (op.flags & OPW_REG);
+        const bool narrow = warp_frames || n <= W || (op.flags & OPW_REG);
         if (!narrow) {
             if (in_run) {
                 o << "    }\n    __syncthreads();\n";
@@ -323,7 +327,7 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             continue;
         }
         if (!in_run) {
-            o << "    if (warp == 0) {\n";
+            o << (warp_frames ? "    {\n" : "    if (warp == 0) {\n");
             in_run = true;
         }
         if (!(op.flags & OPW_REG)) {
@@ -331,9 +335,10 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             o << "      __syncwarp();\n";
             continue;
         }
+        const char *align = warp_frames ? "      __syncthreads();\n" : "";
         if (outline_sub && (op.flags & OPW_REG_ENTER)) {  // the whole subtree is one call
             o << "      " << name << "_sub" << sub_at.at(i) << "(" << in(n) << ", fr.beta, " << op.off
-              << "u);\n      __syncwarp();\n";
+              << "u);\n      __syncwarp();\n" << align;
             while (!(ops[i].flags & OPW_REG_EXIT)) ++i;
             continue;
         }
@@ -346,10 +351,10 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
         i += emit_reg_op(o, ops, i, o0, "        ") - 1;
         if (ops[i].flags & OPW_REG_EXIT) {
             o << "        r.template exit<" << n0 << "u>(fr.beta, " << o0 << "u);\n      }\n"
-              << "      __syncwarp();\n";
+              << "      __syncwarp();\n" << align;
         }
     }
-    if (in_run) o << "    }\n    __syncthreads();\n";
+    if (in_run) o << "    }\n" << (warp_frames ? "    __syncwarp();\n" : "    __syncthreads();\n");
     o << "  }\n};\n";
 }
 
@@ -363,13 +368,17 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
       << ((outline & kOutlineMemory) ? ", memory operations out of line" : "") << "\n"
       << "#include \"polar_ops.cuh\"\n"
       << "namespace polar {\n";
+    const bool warp_frames = shape.frames_per_cta > 1;
     emit_body(o, code, is_i8, shape.smem_stage_max, shape.warp_stage_max, reg_subtree, "GenBody",
-              outline);
+              outline, warp_frames);
     o << "}  // namespace polar\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << shape.threads << ", "
-      << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n"
-      << "  polar::run_frames<" << (is_i8 ? "int8_t" : "float") << ", false, "
-      << (shape.stage_channel ? "true" : "false") << ">(a, polar::GenBody{});\n}\n";
+      << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n";
+    if (warp_frames)
+        o << "  polar::run_warp_frames<" << (is_i8 ? "int8_t" : "float") << ">(a, polar::GenBody{});\n}\n";
+    else
+        o << "  polar::run_frames<" << (is_i8 ? "int8_t" : "float") << ", false, "
+          << (shape.stage_channel ? "true" : "false") << ">(a, polar::GenBody{});\n}\n";
     return o.str();
 }
 

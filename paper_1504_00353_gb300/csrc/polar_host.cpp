@@ -175,8 +175,42 @@ polar_status choose_shape(const polar_code *c, bool is_i8, size_t n_frames, int 
 CompiledKernel *find_compiled(polar_code *c, bool is_i8, const LaunchShape &sh) {
     std::lock_guard<std::mutex> g(c->mu);
     auto it = c->compiled.find(CompiledKey{is_i8, sh.threads, sh.smem_stage_max,
-                                           sh.warp_stage_max, sh.stage_channel});
+                                           sh.warp_stage_max, sh.stage_channel,
+                                           std::max<uint32_t>(sh.frames_per_cta, 1)});
     return it == c->compiled.end() ? nullptr : &it->second;
+}
+
+// The several-frames-per-CTA form of a throughput shape with one warp per
+// frame, when the handle asks for it (polar_code_set_frames_per_cta): F warps,
+// each with its own frame, shared-memory region and scratch; channel read in
+// place. Returns false (sh untouched) when it does not apply.
+bool multi_frame_shape(const polar_code *c, bool is_i8, size_t n_frames, int device,
+                       LaunchShape *sh) {
+    const uint32_t F = c->user[is_i8 ? 1 : 0].frames_per_cta;
+    if (F <= 1 || sh->threads != 32) return false;
+    if (n_frames * 2 <= static_cast<size_t>(device_props(device).sms)) return false;  // batch-1 shape
+    const size_t per_frame =
+        (kernel_smem_bytes(c->N, sh->smem_stage_max, 32, is_i8, false) + 127) / 128 * 128;
+    if (per_frame * F > device_props(device).smem_optin) return false;
+    sh->frames_per_cta = F;
+    sh->threads = 32 * F;
+    sh->stage_channel = 0;
+    sh->smem_bytes = per_frame * F;
+    return true;
+}
+
+// The specialised decoder for this decode, preferring the several-frames-per-CTA
+// shape when one was compiled for it; *sh becomes the shape of what runs.
+CompiledKernel *pick_compiled(polar_code *c, bool is_i8, size_t n_frames, int device,
+                              LaunchShape *sh) {
+    LaunchShape msh = *sh;
+    if (multi_frame_shape(c, is_i8, n_frames, device, &msh)) {
+        if (CompiledKernel *ck = find_compiled(c, is_i8, msh)) {
+            *sh = msh;
+            return ck;
+        }
+    }
+    return find_compiled(c, is_i8, *sh);
 }
 
 int compiled_occupancy(polar_code *c, CompiledKernel *ck, int device, const LaunchShape &sh) {
@@ -200,7 +234,8 @@ polar_status finish_grid(const polar_code *c, bool is_i8, size_t n_frames, int d
     const UserLaunch &u = c->user[is_i8 ? 1 : 0];
     const uint32_t cps = u.ctas_per_sm ? std::min<uint32_t>(u.ctas_per_sm, static_cast<uint32_t>(occ))
                                        : static_cast<uint32_t>(occ);
-    const size_t grid = std::min<size_t>(n_frames, size_t(dp.sms) * cps);
+    const size_t F = std::max<uint32_t>(sh->frames_per_cta, 1);
+    const size_t grid = std::min<size_t>((n_frames + F - 1) / F, size_t(dp.sms) * cps);
     sh->ctas_per_sm = cps;
     sh->grid = static_cast<uint32_t>(std::max<size_t>(grid, 1));
     return POLAR_OK;
@@ -230,10 +265,12 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     LaunchShape sh{};
     polar_status st = choose_shape(c, is_i8, n_frames, device, &sh);
     if (st != POLAR_OK) return st;
-    CompiledKernel *ck = trace ? nullptr : find_compiled(c, is_i8, sh);
+    const LaunchShape sh1 = sh;  // one frame per CTA: what the interpreter runs
+    CompiledKernel *ck = trace ? nullptr : pick_compiled(c, is_i8, n_frames, device, &sh);
     int occ = ck ? compiled_occupancy(c, ck, device, sh) : 0;
     if (occ <= 0) {  // no specialised decoder, or it cannot be resident: interpreter
         ck = nullptr;
+        sh = sh1;
         occ = occupancy(device, is_i8, sh.stage_channel != 0, sh.threads, sh.smem_bytes);
     }
     st = finish_grid(c, is_i8, n_frames, device, occ, &sh);
@@ -268,7 +305,8 @@ polar_status decode_impl(const polar_code_t *code, const void *llr, bool is_i8,
     a.out_row = (c->K + 7) / 8;
 
     void *scratch = nullptr;
-    const size_t scratch_bytes = size_t(sh.grid) * sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
+    const size_t scratch_bytes = size_t(sh.grid) * std::max<uint32_t>(sh.frames_per_cta, 1) *
+                                 sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
     if (scratch_bytes) {
         cudaError_t e = pool_alloc(&scratch, scratch_bytes, device, s);
         if (e != cudaSuccess) {
@@ -588,10 +626,12 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
     LaunchShape sh{};
     polar_status st = choose_shape(c, is_i8 != 0, n, device, &sh);
     if (st != POLAR_OK) return st;
-    CompiledKernel *ck = find_compiled(c, is_i8 != 0, sh);
+    const LaunchShape sh1 = sh;
+    CompiledKernel *ck = pick_compiled(c, is_i8 != 0, n, device, &sh);
     int occ = ck ? compiled_occupancy(c, ck, device, sh) : 0;
     if (occ <= 0) {
         ck = nullptr;
+        sh = sh1;
         occ = occupancy(device, is_i8 != 0, sh.stage_channel != 0, sh.threads, sh.smem_bytes);
     }
     st = finish_grid(c, is_i8 != 0, n, device, occ, &sh);
@@ -603,8 +643,35 @@ polar_status polar_code_get_launch(const polar_code_t *code, int is_i8, size_t n
     if (stage_channel) *stage_channel = sh.stage_channel;
     if (grid) *grid = sh.grid;
     if (smem_bytes) *smem_bytes = sh.smem_bytes;
-    if (scratch_bytes) *scratch_bytes = size_t(sh.grid) * sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
+    if (scratch_bytes)
+        *scratch_bytes = size_t(sh.grid) * std::max<uint32_t>(sh.frames_per_cta, 1) *
+                         sh.scratch_elems_per_cta * (is_i8 ? 1 : 4);
     if (unrolled) *unrolled = ck ? ck->reg_subtree : 0u;
+    return POLAR_OK;
+}
+
+polar_status polar_code_set_frames_per_cta(polar_code_t *code, int is_i8, uint32_t frames) {
+    if (!code || frames > 8 || (frames > 1 && !is_pow2(frames))) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> g(code->mu);
+    code->user[is_i8 ? 1 : 0].frames_per_cta = frames;
+    return POLAR_OK;
+}
+
+polar_status polar_code_get_frames_per_cta(const polar_code_t *code, int is_i8, size_t n_frames,
+                                           uint32_t *frames) {
+    if (!code || !frames) return POLAR_EINVAL;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return POLAR_ECUDA;
+    }
+    polar_code *c = const_cast<polar_code *>(code);
+    const size_t n = std::max<size_t>(n_frames, 1);
+    LaunchShape sh{};
+    const polar_status st = choose_shape(c, is_i8 != 0, n, device, &sh);
+    if (st != POLAR_OK) return st;
+    CompiledKernel *ck = pick_compiled(c, is_i8 != 0, n, device, &sh);
+    *frames = ck ? std::max<uint32_t>(sh.frames_per_cta, 1) : 1u;
     return POLAR_OK;
 }
 
@@ -643,8 +710,10 @@ polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frame
     LaunchShape sh{};
     polar_status st = choose_shape(code, is_i8 != 0, n_frames, device, &sh);
     if (st != POLAR_OK) return st;
+    multi_frame_shape(code, is_i8 != 0, n_frames, device, &sh);
+    const uint32_t F = std::max<uint32_t>(sh.frames_per_cta, 1);
     const CompiledKey key{is_i8 != 0, sh.threads, sh.smem_stage_max, sh.warp_stage_max,
-                          sh.stage_channel};
+                          sh.stage_channel, F};
     if (find_compiled(code, is_i8 != 0, sh)) return POLAR_OK;
     // register subtrees always run inside warp-0 runs
     LaunchShape gsh = sh;
@@ -653,10 +722,11 @@ polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frame
     // the generated kernel is capped so that many fit
     const DeviceProps dp = device_props(device);
     const size_t per_cta = sh.smem_bytes + 1024;
+    const size_t groups = (n_frames + F - 1) / F;
     gsh.ctas_per_sm = static_cast<uint32_t>(std::max<size_t>(
         1, std::min<size_t>({size_t(228 * 1024) / per_cta, size_t(2048 / sh.threads),
                              size_t(dp.max_blocks_per_sm),
-                             size_t(n_frames + dp.sms - 1) / std::max(dp.sms, 1)})));
+                             size_t(groups + dp.sms - 1) / std::max(dp.sms, 1)})));
     if (code->user[is_i8 ? 1 : 0].ctas_per_sm)
         gsh.ctas_per_sm = std::min(gsh.ctas_per_sm, code->user[is_i8 ? 1 : 0].ctas_per_sm);
     CompiledKernel ck;

@@ -36,7 +36,8 @@ struct LaunchShape {
     uint32_t stage_channel;   // 1 = bulk-copy the frame's LLRs to shared memory
     uint32_t grid;
     size_t smem_bytes;
-    size_t scratch_elems_per_cta;  // device alpha scratch per CTA (elements)
+    size_t scratch_elems_per_cta;  // device alpha scratch per frame slot (elements)
+    uint32_t frames_per_cta;       // > 1: one frame per warp, `threads` = 32 x this
 };
 
 struct DeviceState {
@@ -47,12 +48,12 @@ struct DeviceState {
 
 struct UserLaunch {
     uint32_t threads = 0, smem_stage_max = 0, warp_stage_max = 0, ctas_per_sm = 0,
-             stage_channel = 0;
+             stage_channel = 0, frames_per_cta = 0;
 };
 
 // A decoder specialised to one code and launch shape (generated CUDA source
-// compiled with NVRTC): key = (is_i8, threads, S, W, stage_channel).
-using CompiledKey = std::tuple<bool, uint32_t, uint32_t, uint32_t, uint32_t>;
+// compiled with NVRTC): key = (is_i8, threads, S, W, stage_channel, frames per CTA).
+using CompiledKey = std::tuple<bool, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>;
 struct CompiledKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;

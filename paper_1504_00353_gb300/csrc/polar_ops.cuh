@@ -487,8 +487,9 @@ __device__ __forceinline__ void op_rep(const T *in, T *tmp, uint32_t *beta, uint
         src = tmp;
         len = m;
     }
-    if (threadIdx.x < 32) {
-        const uint32_t lane = threadIdx.x;
+    // the last folds: warp 0 of the CTA (CTA group), or the calling warp
+    if (!Grp::kCta || threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x & 31u;
         Acc x;
         uint32_t cur;
         if (len == 64) {
@@ -692,6 +693,66 @@ __device__ __forceinline__ void run_frames(const KernelArgs &a, const Body &body
             bulk_load((it & 1u) ? chan1 : chan0, llr + (f + 2 * G) * a.N, chan_bytes,
                       &mbar[it & 1u]);
         }
+    }
+}
+
+// Persistent loop with several frames per CTA, one per warp: the CTA's
+// F = blockDim.x / 32 warps decode F frames side by side, each with its own
+// shared-memory region and scratch, running the same straight-line decoder
+// (every group operation of the body is warp-level). Barriers in the body keep
+// the warps in step, so that they share the instructions they fetch. In the
+// last group, warps without a frame decode frame 0 again and store nothing, so
+// that every warp passes the same barriers.
+template <typename T, class Body>
+__device__ __forceinline__ void run_warp_frames(const KernelArgs &a, const Body &body) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout L(a.N, a.S, sizeof(T), false);
+    const size_t per_frame = align_up(L.total, 128);
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5, F = blockDim.x >> 5;
+    unsigned char *base = smem + size_t(w) * per_frame;
+    Frame<T> fr;
+    fr.s_alpha = reinterpret_cast<T *>(base + L.alpha);
+    fr.beta = reinterpret_cast<uint32_t *>(base + L.beta);
+    fr.rkey = reinterpret_cast<unsigned long long *>(base + L.rkey);
+    fr.rpar = reinterpret_cast<uint32_t *>(base + L.rpar);
+    fr.g_alpha = a.gscratch
+                     ? static_cast<T *>(a.gscratch) + (size_t(blockIdx.x) * F + w) * a.gstride
+                     : nullptr;
+    fr.N = a.N;
+    fr.S = a.S;
+    const T *llr = static_cast<const T *>(a.llr);
+    const size_t groups = (a.n_frames + F - 1) / F;
+    for (size_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        const size_t f = g * F + w;
+        const bool valid = f < a.n_frames;
+        fr.chan = llr + (valid ? f : 0) * a.N;
+        body(fr, nullptr);
+        if (valid) {
+            uint8_t *out = a.out + f * a.out_row;
+            for (uint32_t u = lane; u < a.KW; u += 32u) {
+                const uint32_t lo = u << 5;
+                const uint32_t hi = min(lo + 32u, a.K);
+                uint32_t acc = 0;
+                for (uint32_t wd = __ldg(a.ext_wstart + u); wd < a.NW; ++wd) {
+                    const uint32_t pre = __ldg(a.ext_pre + wd);
+                    if (pre >= hi) break;
+                    const uint32_t m = __ldg(a.ext_mask + wd);
+                    if (!m) continue;
+                    const uint32_t e = pext32(fr.beta[wd], m);
+                    const int pos = static_cast<int>(pre) - static_cast<int>(lo);
+                    acc |= pos >= 0 ? (e << pos) : (e >> (-pos));
+                }
+                if (hi - lo < 32) acc &= (1u << (hi - lo)) - 1u;
+                const uint32_t nb = min(4u, a.out_row - 4u * u);
+                uint8_t *dst = out + 4u * u;
+                if (nb == 4 && (reinterpret_cast<uintptr_t>(dst) & 3u) == 0) {
+                    *reinterpret_cast<uint32_t *>(dst) = acc;
+                } else {
+                    for (uint32_t b = 0; b < nb; ++b) dst[b] = static_cast<uint8_t>(acc >> (8 * b));
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -30,7 +30,8 @@ EXPORTS = [
     "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
     "polar_server_progress", "polar_server_destroy", "polar_random_info",
     "polar_encode_systematic_device", "polar_channel_awgn", "polar_count_errors", "polar_fer_run",
-    "polar_decode_host", "polar_selftest_bounded_wait",
+    "polar_decode_host", "polar_selftest_bounded_wait", "polar_code_set_frames_per_cta",
+    "polar_code_get_frames_per_cta",
 ]
 
 # struct polar_request
@@ -89,6 +90,8 @@ def _load():
         "polar_random_info": ([vp, vp, sz, ctypes.c_uint64, ctypes.c_uint64, vp], st),
         "polar_decode_host": ([vp, st, vp, vp, sz, sz], st),
         "polar_selftest_bounded_wait": ([vp, u32, vp], st),
+        "polar_code_set_frames_per_cta": ([vp, st, u32], st),
+        "polar_code_get_frames_per_cta": ([vp, st, sz, u32p], st),
         "polar_encode_systematic_device": ([vp, vp, vp, sz, vp], st),
         "polar_channel_awgn": ([vp, vp, vp, st, sz, ctypes.c_float, ctypes.c_uint64,
                                 ctypes.c_uint64, vp], st),
@@ -304,7 +307,18 @@ def polar_code_get_launch(code: PolarCode, is_i8: bool, n_frames: int) -> dict:
     d = {k: x.value for k, x in zip(keys, v)}
     d["smem_bytes"], d["scratch_bytes"] = s[0].value, s[1].value
     d["unrolled"] = unrolled.value
+    f = ctypes.c_uint32()
+    _check(_lib.polar_code_get_frames_per_cta(code.handle, int(bool(is_i8)), n_frames,
+                                              ctypes.byref(f)), "polar_code_get_frames_per_cta")
+    d["frames_per_cta"] = f.value
     return d
+
+
+def polar_code_set_frames_per_cta(code: PolarCode, is_i8: bool, frames: int):
+    """Several frames per CTA, one per warp (2, 4, 8; 0/1 = one), for the
+    specialised decoder of one-warp-per-frame shapes (compile afterwards)."""
+    _check(_lib.polar_code_set_frames_per_cta(code.handle, int(bool(is_i8)), frames),
+           "polar_code_set_frames_per_cta")
 
 
 COMPILE_OUTLINE_SUBTREES, COMPILE_OUTLINE_MEMORY, COMPILE_COMPACT, COMPILE_FULL = 1, 2, 3, 4

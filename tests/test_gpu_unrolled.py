@@ -180,3 +180,63 @@ def test_decode_from_host_buffers(i8):
         assert np.array_equal(got.numpy(), want), chunk
     got = polar.polar_decode_host(code, y)  # pageable numpy input also works
     assert np.array_equal(got.numpy(), want)
+
+
+@pytest.mark.parametrize("i8", [False, True])
+@pytest.mark.parametrize("F", [2, 4])
+def test_frames_per_cta(i8, F):
+    """Several frames per CTA, one per warp: the oracle's bits, including a
+    ragged last group; the interpreter and batch-1 shapes keep one frame per CTA."""
+    mask, d, llr = _cases.frames(1024, 512, 2.5, 1001, seed=39, distinct=200)
+    y = synth.quantize_i8(llr) if i8 else llr
+    code = polar.polar_code_create(1024, 512, mask)
+    polar.polar_code_set_launch(code, i8, threads=32, stage_channel=2)
+    polar.polar_code_set_frames_per_cta(code, i8, F)
+    assert polar.polar_code_get_launch(code, i8, 1001)["frames_per_cta"] == 1  # not compiled yet
+    assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y))
+    polar.polar_code_compile(code, i8, 1001)
+    launch = polar.polar_code_get_launch(code, i8, 1001)
+    assert launch["frames_per_cta"] == F and launch["threads"] == 32 * F and launch["unrolled"]
+    assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y))
+    assert polar.polar_code_get_launch(code, i8, 1)["frames_per_cta"] == 1
+    assert np.array_equal(decode(code, y[:1], i8), oracle.decode_batch(mask, y[:1]))
+
+
+def test_frames_per_cta_n32768_sampled():
+    mask, d, llr = _cases.frames(32768, 29492, 4.0, 4096, seed=40, distinct=64)
+    y = synth.quantize_i8(llr)
+    code = polar.polar_code_create(32768, 29492, mask)
+    polar.polar_code_set_launch(code, True, threads=32, smem_stage_max=256, stage_channel=2)
+    polar.polar_code_set_frames_per_cta(code, True, 4)
+    polar.polar_code_compile(code, True, 4096)
+    assert polar.polar_code_get_launch(code, True, 4096)["frames_per_cta"] == 4
+    got = decode(code, y, True)
+    sample = np.sort(np.random.default_rng(6).choice(4096, 40, replace=False))
+    assert np.array_equal(got[sample], oracle.decode_batch(mask, y, frames=sample))
+    with pytest.raises(polar.PolarError):
+        polar.polar_code_set_frames_per_cta(code, True, 3)
+
+
+@pytest.mark.parametrize("F", [2, 4])
+def test_frames_per_cta_memory_level_nodes(F):
+    """Repetition, SPC and Rate-1 nodes wider than the warp threshold run in
+    memory on each warp's own frame (the top of a (4096, *) code built from one
+    wide node of each kind)."""
+    h = 1024
+    rep = np.ones(h, np.uint8)
+    rep[-1] = 0
+    spc = np.zeros(h, np.uint8)
+    spc[0] = 1
+    mask = np.concatenate([rep, spc, np.zeros(h, np.uint8), rep])
+    N, K = mask.size, int((mask == 0).sum())
+    rng = np.random.default_rng(41 + F)
+    for i8 in (False, True):
+        y = rng.integers(-127, 128, (257, N)).astype(np.int8) if i8 else \
+            (rng.standard_normal((257, N)) * 3).astype(np.float32)
+        code = polar.polar_code_create(N, K, mask)
+        polar.polar_code_set_launch(code, i8, threads=32, smem_stage_max=256, warp_stage_max=256,
+                                    stage_channel=2)
+        polar.polar_code_set_frames_per_cta(code, i8, F)
+        polar.polar_code_compile(code, i8, 257, 256)
+        assert polar.polar_code_get_launch(code, i8, 257)["frames_per_cta"] == F
+        assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y))
