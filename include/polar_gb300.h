@@ -185,8 +185,10 @@ polar_status polar_decode_trace(const polar_code_t *code, const void *llr, int i
 
 /* Launch shape for one LLR type (is_i8 = 0 float32, 1 int8). 0 in any field
  * restores the automatic choice for that field.
- *   threads          threads per CTA (one CTA decodes one frame at a time),
- *                    multiple of 32, <= 1024.
+ *   threads          threads per frame: per CTA, since a CTA decodes one frame
+ *                    at a time, unless several frames per CTA are set
+ *                    (polar_code_set_frames_per_cta, threads = 32); multiple
+ *                    of 32, <= 1024.
  *   smem_stage_max   largest alpha stage (node size) kept in shared memory;
  *                    power of two >= 64. Wider stages live in per-CTA device
  *                    scratch.
