@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--workload", default="n32768_k29492_4.0db", choices=sorted(synth.WORKLOADS))
     p.add_argument("--batch", type=int, default=0, help="frames per step per GPU (0: workload's)")
     p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--reference-seconds", type=float, default=60.0,
+                   help="reference arm: CPU seconds of oracle work over all timed steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--latency-frames", type=int, default=200)
     p.add_argument("--no-e2e", action="store_true")
@@ -273,7 +275,8 @@ def run_reference(args, world, rank):
         time_oracle(mask, llr[: min(sample, 16)], budget_cpu_s=0.5)
     tot_frames, tot_s, T = 0, 0.0, 1
     for _ in range(args.steps):
-        f, s, T = time_oracle(mask, llr, budget_cpu_s=max(2.0, 60.0 / max(args.steps, 1)))
+        f, s, T = time_oracle(mask, llr, budget_cpu_s=max(
+            0.5, args.reference_seconds / max(args.steps, 1)))
         tot_frames += f
         tot_s += s
     gbps = K * tot_frames / tot_s / 1e9
