@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--latency-frames", type=int, default=200)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-mixed", action="store_true",
+                   help="leave out the mixed-length batch block of the default line")
+    p.add_argument("--no-serve", action="store_true",
+                   help="leave out the serving block of the default line")
     p.add_argument("--no-variant", action="store_true", help="skip the other LLR type")
     p.add_argument("--interpreter", action="store_true",
                    help="time the operation-list interpreter instead of the specialised decoder")
@@ -201,6 +205,17 @@ def profile_traffic(workload, dtype):
     return float(m.group(1))
 
 
+def profile_smem(workload, dtype):
+    """Shared-memory bytes per launch (ncu smsp__sass_data_bytes_mem_shared.sum)
+    from the committed summary of the specialised decoder, under the same
+    source-hash rule as profile_traffic."""
+    path = os.path.join(ROOT, "profiles", f"fastssc_unrolled_{dtype}_{workload}.md")
+    if not os.path.exists(path) or profile_traffic(workload, dtype) is None:
+        return None
+    m = re.search(r"smem_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
+    return float(m.group(1)) if m else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -252,6 +267,61 @@ def time_oracle(mask, llr, budget_cpu_s=16.0, threads=None):
     return frames * passes, dt, len(ths)
 
 
+def oracle_baseline(mask, llr, reps=10, budget_cpu_s=12.0):
+    """The CPU oracle timed the way the paper times its decoders (Sec. III,
+    methodology: repeated runs, one core), and on every host core: the median
+    of `reps` repetitions of each, over a bounded sample of the workload's
+    frames (the first frames of the seeded batch). Returns the cpu_baseline
+    dict and the oracle's bits for frames [0, m) with m (for the parity sample)."""
+    import oracle
+    oracle.build()
+    n_total = llr.shape[0]
+    T = max(1, min(os.cpu_count() or 1, 64))
+    t0 = time.perf_counter()
+    oracle.decode_batch(mask, llr[:1])
+    per = max(time.perf_counter() - t0, 1e-6)
+    # one core: a third of the CPU budget
+    m1 = int(np.clip(budget_cpu_s / 3 / reps / per, 1, n_total))
+    st, bits = [], None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        b = oracle.decode_batch(mask, llr, frames=slice(0, m1))
+        st.append(time.perf_counter() - t0)
+        bits = b if bits is None else bits
+    # every core: T threads on disjoint slices, the rest of the budget
+    m2 = int(np.clip(2 * budget_cpu_s / 3 / reps / per / T, 1, max(1, n_total // T)))
+    chunks = [slice(i * m2, (i + 1) * m2) for i in range(T) if (i + 1) * m2 <= n_total]
+    at, errs = [], []
+
+    def work(ix):
+        try:
+            oracle.decode_batch(mask, llr, frames=ix)
+        except Exception as e:  # pragma: no cover
+            errs.append(e)
+
+    for _ in range(reps):
+        ths = [threading.Thread(target=work, args=(c,)) for c in chunks]
+        t0 = time.perf_counter()
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        at.append(time.perf_counter() - t0)
+    if errs:
+        raise errs[0]
+    K = int((np.asarray(mask) == 0).sum())
+    one = K * m1 / statistics.median(st) / 1e9
+    allc = K * m2 * len(chunks) / statistics.median(at) / 1e9
+    d = {"value": allc, "unit": "Gbps", "cores": len(chunks), "kind": "oracle",
+         "single_thread": {"value": one, "unit": "Gbps", "cores": 1,
+                           "frame_us": 1e6 * statistics.median(st) / m1},
+         "reps": reps, "statistic": "median", "nproc": os.cpu_count(),
+         "sample": (f"plain C Fast-SSC oracle; one core: frames 0..{m1 - 1} of the seeded batch "
+                    f"x {reps} repetitions; all cores: {len(chunks)} threads x {m2} frames "
+                    f"x {reps} repetitions; medians")}
+    return d, bits, m1
+
+
 # ---------------------------------------------------------------- arms
 
 def run_reference(args, world, rank):
@@ -293,22 +363,6 @@ def run_reference(args, world, rank):
         "e2e": {"value": gbps, "unit": "Gbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-# Launch shapes of the specialised decoders, chosen by measurement on GB300
-# (threads per CTA, largest shared-memory alpha stage, warp-run threshold,
-# channel staging: 2 = read in place).
-TUNED = {
-    ("n32768_k29492_4.0db", "f32"): dict(threads=128, smem_stage_max=2048, warp_stage_max=2048,
-                                         stage_channel=2),
-    ("n32768_k29492_4.0db", "i8"): dict(threads=32, smem_stage_max=512, stage_channel=2),
-    ("n1024_k512_2.5db", "f32"): dict(threads=32, stage_channel=2),
-    ("n1024_k512_2.5db", "i8"): dict(threads=32, stage_channel=2),
-}
-# Batch-1 (latency) shapes: one CTA, every stage in shared memory.
-TUNED_LATENCY = {
-    "n32768_k29492_4.0db": dict(threads=256, warp_stage_max=1024),
-}
 
 
 def element_ops(code):
@@ -363,7 +417,7 @@ def run_native(args, world, rank, local):
         """Code handle with its specialised decoder compiled (untimed set-up)."""
         i8 = dtype == "i8"
         code = polar.polar_code_create(N, K, mask)
-        shape, _ = tuned_or(N, K, mask, dtype, TUNED.get((args.workload, dtype), {}))
+        shape, _ = tuned_or(N, K, mask, dtype)
         shape.setdefault("stage_channel", 2)
         compile_shape(code, dtype, shape, batch, args.interpreter, args.compile_form)
         return code
@@ -378,8 +432,9 @@ def run_native(args, world, rank, local):
         # (each step streams more than L2 before a buffer is reused).
         n_buf = 1 if in_bytes > 2 * L2_BYTES else int(np.ceil(3 * L2_BYTES / in_bytes)) + 1
         base = torch.from_numpy(llr_by_dtype[dtype]).to(dev)
-        bufs = [base] + [base[torch.randperm(batch, generator=torch.Generator().manual_seed(i))
-                              .to(dev)].contiguous() for i in range(1, n_buf)]
+        perms = [torch.arange(batch)] + [torch.randperm(batch, generator=torch.Generator().manual_seed(i))
+                                         for i in range(1, n_buf)]
+        bufs = [base] + [base[perms[i].to(dev)].contiguous() for i in range(1, n_buf)]
         out = torch.empty((batch, row), dtype=torch.uint8, device=dev)
         # sanity gate against the transmitted bits (not a parity test)
         decode(code, bufs[0], out)
@@ -389,8 +444,12 @@ def run_native(args, world, rank, local):
         total_ms, launch_ms = device_timed(torch, stream, lambda i: decode(code, bufs[i % n_buf], out),
                                            steps, warmup, world)
         polar.polar_code_check(code)
+        # the output of the last timed launch, rows in the order of frames of the batch
+        last = (steps - 1) % n_buf
+        timed_out = np.empty((batch, row), np.uint8)
+        timed_out[perms[last].numpy()] = out.cpu().numpy()
         return dict(code=code, decode=decode, bufs=bufs, out=out, n_buf=n_buf, in_bytes=in_bytes,
-                    total_ms=total_ms, launch_ms=launch_ms, fer=fer,
+                    total_ms=total_ms, launch_ms=launch_ms, fer=fer, timed_out=timed_out,
                     gbps=world * batch * K * steps / (total_ms * 1e-3) / 1e9,
                     launch=polar.polar_code_get_launch(code, i8, batch))
 
@@ -412,17 +471,15 @@ def run_native(args, world, rank, local):
     e2e_gbps, e2e_chunk = None, None
     if not args.no_e2e:
         e2e_steps = max(3, args.steps // 2)
-        for chunk in sorted({max(1, batch // 2), max(1, batch // 4), max(1, batch // 8)}):
-            for _ in range(2):
-                polar.polar_decode_host(code, host_in, host_out, chunk)
-            barrier(world)
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                polar.polar_decode_host(code, host_in, host_out, chunk)
-            e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-            g = world * batch * K * e2e_steps / e2e_s / 1e9
-            if e2e_gbps is None or g > e2e_gbps:
-                e2e_gbps, e2e_chunk = g, chunk
+        for _ in range(2):
+            polar.polar_decode_host(code, host_in, host_out)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            polar.polar_decode_host(code, host_in, host_out)
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        e2e_gbps = world * batch * K * e2e_steps / e2e_s / 1e9
+        e2e_chunk = "library default"
         decode(code, r["bufs"][0], out)  # the same frames through the device-buffer call
         torch.cuda.synchronize()
         assert np.array_equal(host_out.numpy(), out.cpu().numpy()), "host-buffer decode differs"
@@ -435,7 +492,7 @@ def run_native(args, world, rank, local):
     if nlat:
         i8 = main == "i8"
         lcode = polar.polar_code_create(N, K, mask)
-        lshape, _ = tuned_or(N, K, mask, main, TUNED_LATENCY.get(args.workload, {}), latency=True)
+        lshape, _ = tuned_or(N, K, mask, main, latency=True)
         compile_shape(lcode, main, lshape, 1, args.interpreter, args.compile_form)
         one_in = torch.empty((1, N), dtype=r["bufs"][0].dtype, device=dev)
         one_out = torch.empty((1, row), dtype=torch.uint8, device=dev)
@@ -471,15 +528,27 @@ def run_native(args, world, rank, local):
     alg_bytes = batch * (N * es + row)
     achieved = alg_bytes / (r["launch_ms"] * 1e-3) / 1e9
     ops = element_ops(code) * batch
-    alu_peak = 152 * 128 * 2.07e9  # lanes x max SM clock: one element-op per lane per clock
+    # element-op roof: one element operation per lane per clock on every SM (the
+    # SM count from the device, the clock at its maximum and at the median seen
+    # under load during the timed region)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    med_mhz = (clocks or {}).get("sm_mhz") or max_mhz
+    alu_peak = sms * 128 * max_mhz * 1e6
     t_hbm = alg_bytes / (hbm_peak * 1e9)
     t_alu = ops / alu_peak
+    smem = profile_smem(args.workload, main)
+    smem_peak = sms * 128 * max_mhz * 1e6  # bytes per second: 128 B per clock per SM
     line = {
         "metric": METRIC, "value": r["gbps"], "unit": "Gbps", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": (r["gbps"] / PAPER_GBPS[(args.workload, main)]
                         if (args.workload, main) in PAPER_GBPS else None),
+        "vs_baseline_basis": ("the paper's own number for this code and LLR type (Tables 2-3: "
+                              "unrolled decoder on one core of an Intel i7-4770S at 3.1 GHz); "
+                              "context from other hardware, not the target"
+                              if (args.workload, main) in PAPER_GBPS else None),
         "dtype": main, "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "K": K, "global_batch": batch * world,
                    "batch_per_gpu": batch, "ebn0_db": wl["ebn0_db"], "llr": main,
@@ -500,12 +569,23 @@ def run_native(args, world, rank, local):
                      "peak": hbm_peak if t_hbm >= t_alu else alu_peak / 1e12,
                      "unit": "GB/s" if t_hbm >= t_alu else "Tops/s",
                      "frac": (t_hbm if t_hbm >= t_alu else t_alu) / (r["launch_ms"] * 1e-3),
-                     "peak_kind": peak_kind,
+                     "peak_kind": (peak_kind if t_hbm >= t_alu else
+                                   f"{sms} SMs x 128 lanes x {max_mhz:.0f} MHz (device query, "
+                                   "maximum SM clock)"),
                      "traffic": profile_traffic(args.workload, main),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "element_ops_per_launch": ops,
                      "hbm_frac": t_hbm / (r["launch_ms"] * 1e-3),
+                     "hbm_peak_gbs": hbm_peak,
                      "alu_frac": t_alu / (r["launch_ms"] * 1e-3),
+                     "alu_frac_at_median_clock": t_alu * max_mhz / med_mhz / (r["launch_ms"] * 1e-3),
+                     "smem": None if smem is None else {
+                         "bound": "diagnostic", "bytes_per_launch": smem,
+                         "achieved": smem / (r["launch_ms"] * 1e-3) / 1e9,
+                         "peak": smem_peak / 1e9, "unit": "GB/s",
+                         "frac": smem / (r["launch_ms"] * 1e-3) / smem_peak,
+                         "source": "ncu smsp__sass_data_bytes_mem_shared.sum of the committed "
+                                   "profile; peak = SMs x 128 B/clk x maximum SM clock"},
                      "launch_ms": r["launch_ms"]},
         "clocks": clocks,
     }
@@ -514,12 +594,20 @@ def run_native(args, world, rank, local):
                                     "ms_per_step": alt["total_ms"] / max(3, args.steps // 2),
                                     "launch": alt["launch"], "fer_check": alt["fer"]}}
     if rank == 0 and not args.no_cpu_baseline:
-        f, s_, T = time_oracle(mask, llr_by_dtype[main])
-        line["cpu_baseline"] = {"value": K * f / s_ / 1e9, "unit": "Gbps", "cores": T,
-                                "kind": "oracle",
-                                "sample": f"{f} frames of {args.workload} ({main}), "
-                                          f"plain C Fast-SSC oracle, {T} host threads, "
-                                          f"{s_:.1f} s wall"}
+        cb, obits, m = oracle_baseline(mask, llr_by_dtype[main])
+        cb["sample"] = f"{args.workload} ({main}); " + cb["sample"]
+        line["cpu_baseline"] = cb
+        # the same frames of the last timed launch, decoded by the GPU, against
+        # the oracle's bits from the timing above
+        eq = np.all(r["timed_out"][:m] == obits, axis=1)
+        line["parity_sample"] = {"frames": int(m), "equal": bool(eq.all()),
+                                 "frames_differing": int((~eq).sum()),
+                                 "what": "bits of the last timed launch vs the CPU oracle, "
+                                         f"frames 0..{m - 1} of the batch"}
+    if rank == 0 and world == 1 and not args.no_mixed:
+        line["mixed"] = mixed_block(args)
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["serve"] = serve_block(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -552,46 +640,19 @@ def mixed_inputs(n, dtype, seed, ebn0=None, ebn0_range=None):
     return masks, cid, llr, bits
 
 
-def tuned_or(N, K, mask, dtype, default, latency=False):
-    """Launch shape from the autotuner's table for this GPU, else `default`."""
+def tuned_or(N, K, mask, dtype, default=None, latency=False):
     from paper_1504_00353_gb300 import autotune
-    try:
-        e = autotune.lookup(N, K, mask, dtype, latency=latency)
-    except Exception:  # no table or no device name
-        e = None
-    if not e:
-        return dict(default), "default"
-    return {k: e[k] for k in autotune.SHAPE_KEYS if k in e}, "tuned"
-
-
-COMPILE_FORM = {"auto": 0, "subtrees": 1, "memory": 2, "compact": 3, "full": 4}
+    return autotune.shape_for(N, K, mask, dtype, latency=latency, default=default)
 
 
 def compile_shape(code, dtype, shape, n_frames, interpreter=False, form="auto"):
-    """Set a launch shape (dict of polar_code_set_launch arguments, plus
-    reg_subtree) and compile the specialised decoder unless timing the
-    interpreter."""
-    from paper_1504_00353_gb300 import polar
-    sh = dict(shape)
-    reg = sh.pop("reg_subtree", 0)
-    fpc = sh.pop("frames_per_cta", 1)
-    if sh:
-        polar.polar_code_set_launch(code, dtype == "i8", **sh)
-    polar.polar_code_set_frames_per_cta(code, dtype == "i8", fpc)
-    if not interpreter:
-        polar.polar_code_compile(code, dtype == "i8", n_frames, reg, COMPILE_FORM[form])
+    from paper_1504_00353_gb300 import autotune
+    autotune.configure(code, dtype, shape, n_frames, interpreter, form)
 
 
 def batch_shape(dtype):
     from paper_1504_00353_gb300 import autotune
-    try:
-        e = autotune.load_table().get(autotune.device_name(), {}).get(f"mixed_{dtype}")
-    except Exception:
-        e = None
-    if e:
-        return dict(threads=e["threads"], smem_stage_max=e["smem_stage_max"],
-                    warp_stage_max=e["warp_stage_max"], ctas_per_sm=e.get("ctas_per_sm", 0)), "tuned"
-    return dict(threads=32, smem_stage_max=None, warp_stage_max=None, ctas_per_sm=0), "default"
+    return autotune.batch_shape(dtype)
 
 
 def run_mixed(args):
@@ -617,8 +678,8 @@ def run_mixed(args):
     codes, outs, bufs, shapes = [], [], [], []
     for c, (N, K) in enumerate(nk):
         shape, src = tuned_or(N, K, masks[c], dtype,
-                              dict(threads=32, smem_stage_max=512, warp_stage_max=2048,
-                                   ctas_per_sm=0))
+                              default=dict(threads=32, smem_stage_max=512, warp_stage_max=2048,
+                                           ctas_per_sm=0))
         shape.setdefault("stage_channel", 2)
         code = polar.polar_code_create(N, K, masks[c])
         compile_shape(code, dtype, shape, llr[c].shape[0])
@@ -889,6 +950,217 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- blocks of the default line
+
+def device_mixed(torch, polar, codes, cid, dtype, seed, ebn0=None, ebn0_range=None):
+    """Frames of the mixed code set generated on the device by the library's
+    chain: Philox information bits, the device systematic encoder and the BPSK-AWGN
+    channel (one Eb/N0, or one drawn per frame from ebn0_range). Frames are
+    stored code by code in one flat LLR buffer. Returns (flat LLRs, per-code
+    views [m_c, N_c], per-code info bits [m_c, ceil(K_c/8)], per-code element
+    offsets of the views in flat)."""
+    dt = torch.int8 if dtype == "i8" else torch.float32
+    counts = [int((cid == c).sum()) for c in range(len(codes))]
+    sizes = [m * code.N for m, code in zip(counts, codes)]
+    flat = torch.empty(sum(sizes), dtype=dt, device="cuda")
+    views, infos, bases = [], [], []
+    base = 0
+    rng = np.random.default_rng(seed)
+    for c, (code, m) in enumerate(zip(codes, counts)):
+        v = flat[base: base + m * code.N].view(m, code.N)
+        info = torch.empty((m, code.out_row), dtype=torch.uint8, device="cuda")
+        cw = torch.empty((m, (code.N + 7) // 8), dtype=torch.uint8, device="cuda")
+        if m:
+            polar.polar_random_info(code, info, seed + c)
+            polar.polar_encode_systematic_device(code, info, cw)
+            if ebn0_range is None:
+                polar.polar_channel_awgn(code, cw, v, ebn0, seed + 100 + c)
+            else:
+                for j, db in enumerate(rng.uniform(*ebn0_range, m)):
+                    polar.polar_channel_awgn(code, cw[j:j + 1], v[j:j + 1], float(db), seed + 100 + c,
+                                             frame0=j)
+        views.append(v)
+        infos.append(info)
+        bases.append(base)
+        base += m * code.N
+    torch.cuda.synchronize()
+    return flat, views, infos, bases
+
+
+def mixed_block(args, n=None, steps=10, warmup=3):
+    """Config-3 comparison for the default line: 65,536 int8 frames of the five
+    mixed codes, one persistent launch of the mixed-batch decoder replayed from a
+    CUDA graph, against one launch per code with each code's own tuned decoder.
+    Inputs come from the library's device chain (seeded)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1504_00353_gb300 import autotune, polar
+    dtype = "i8"
+    n = n or synth.MIXED_FRAMES
+    nk = synth.MIXED_CODES
+    masks = [synth.frozen_mask(N, K, synth.MIXED_DESIGN_DB) for N, K in nk]
+    codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
+    cid = np.random.default_rng(3).integers(0, len(nk), n)
+    counts = [int((cid == c).sum()) for c in range(len(nk))]
+    shapes = []
+    for c, (N, K) in enumerate(nk):
+        sh, src = autotune.shape_for(N, K, masks[c], dtype,
+                                     default=dict(threads=32, smem_stage_max=512,
+                                                  warp_stage_max=2048, ctas_per_sm=0))
+        sh.setdefault("stage_channel", 2)
+        shapes.append((sh, src))
+    bshape, bsrc = autotune.batch_shape(dtype)
+    t_c = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=6) as ex:
+        futs = [ex.submit(autotune.configure, codes[c], dtype, shapes[c][0], counts[c])
+                for c in range(len(nk))]
+        # the batch kernel gets handles of its own (compiled concurrently)
+        bcodes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
+        fb = ex.submit(polar.polar_batch_create, bcodes, True, bshape["threads"],
+                       bshape["smem_stage_max"], bshape["warp_stage_max"], bshape["ctas_per_sm"])
+        for f in futs:
+            f.result()
+        batch = fb.result()
+    t_c = time.perf_counter() - t_c
+    flat, views, infos, bases = device_mixed(torch, polar, codes, cid, dtype, seed=3,
+                                             ebn0=synth.MIXED_DESIGN_DB)
+    orow = [code.out_row for code in codes]
+    obase = np.concatenate([[0], np.cumsum([m * r for m, r in zip(counts, orow)])])
+    out_b = torch.zeros(int(obase[-1]), dtype=torch.uint8, device="cuda")
+    outs = [out_b.new_zeros((m, r)) for m, r in zip(counts, orow)]
+    # descriptors, longest code first (the order CTAs claim frames in)
+    ids, lo, oo = [], [], []
+    for c in sorted(range(len(nk)), key=lambda c: -nk[c][0]):
+        m = counts[c]
+        ids.append(np.full(m, c, np.int32))
+        lo.append(bases[c] + np.arange(m, dtype=np.int64) * nk[c][0])
+        oo.append(obase[c] + np.arange(m, dtype=np.int64) * orow[c])
+    d_ids, d_lo, d_oo = (torch.from_numpy(np.concatenate(x)).cuda() for x in (ids, lo, oo))
+    dec = polar.polar_decode_i8
+
+    def plain(_):
+        for c in range(len(nk)):
+            dec(codes[c], views[c], outs[c])
+
+    stream = torch.cuda.current_stream()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        polar.polar_batch_decode(batch, d_ids, d_lo, d_oo, flat, out_b, stream=s2)
+    stream.wait_stream(s2)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        polar.polar_batch_decode(batch, d_ids, d_lo, d_oo, flat, out_b)
+    out_b.zero_()
+    plain(0)
+    graph.replay()
+    torch.cuda.synchronize()
+    agree = bool(torch.equal(out_b, torch.cat([o.reshape(-1) for o in outs])))
+    ferr = sum(int((outs[c] != infos[c]).any(dim=1).sum()) for c in range(len(nk)))
+    with ClockSampler(0) as clk:
+        plain_ms, _ = device_timed(torch, stream, plain, steps, warmup, 1)
+        batched_ms, _ = device_timed(torch, stream, lambda i: graph.replay(), steps, warmup, 1)
+    info_bits = sum(m * K for m, (N, K) in zip(counts, nk))
+    return {
+        "what": "one persistent launch over all frames, replayed from a CUDA graph (batched) "
+                "vs one launch per code (plain), same device buffers",
+        "frames": n, "codes": nk, "frames_per_code": counts, "llr": dtype,
+        "design_db": synth.MIXED_DESIGN_DB, "ebn0_db": synth.MIXED_DESIGN_DB,
+        "inputs": f"{flat.numel() * flat.element_size() / 2**20:.0f} MiB on the device (larger "
+                  "than L2), generated by the library's Philox/encoder/AWGN chain, stored code by code",
+        "batched": {"gbps": info_bits * steps / (batched_ms * 1e-3) / 1e9,
+                    "step_ms": batched_ms / steps, "launches_per_step": 1, "cuda_graph": True,
+                    "shape": dict(bshape, source=bsrc), "launch": polar.polar_batch_info(batch)},
+        "plain": {"gbps": info_bits * steps / (plain_ms * 1e-3) / 1e9,
+                  "step_ms": plain_ms / steps, "launches_per_step": len(nk),
+                  "shapes": [dict(sh, source=src) for sh, src in shapes]},
+        "batched_over_plain": plain_ms / batched_ms,
+        "bits_agree": agree, "frame_errors": ferr, "compile_s": t_c, "steps": steps,
+        "warmup": warmup, "clocks": clk.summary(),
+    }
+
+
+def serve_block(args, loads=(1, 10, 50, 200), seconds=0.5, max_frames=40_000):
+    """Config-4 comparison for the default line: Poisson arrivals of float32
+    frames of the mixed codes (Eb/N0 uniform in [2.0, 4.5] dB per frame) through
+    the serving loop (continuous batching: overlapping launches, admission by
+    device-memory budget) against a plain queue (one launch per code, one batch
+    at a time), the request pool resident in HBM. One run per load; the full
+    comparison with two runs per cell and a pinned-host pool is --mode serve."""
+    import torch
+
+    from paper_1504_00353_gb300 import autotune, polar
+    nk = synth.MIXED_CODES
+    P = 16384
+    masks = [synth.frozen_mask(N, K, synth.MIXED_DESIGN_DB) for N, K in nk]
+    codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
+    cid = np.random.default_rng(4).integers(0, len(nk), P)
+    flat, views, infos, bases = device_mixed(torch, polar, codes, cid, "f32", seed=4,
+                                             ebn0_range=(2.0, 4.5))
+    counts = [int((cid == c).sum()) for c in range(len(nk))]
+    orow = [code.out_row for code in codes]
+    obase = np.concatenate([[0], np.cumsum([m * r for m, r in zip(counts, orow)])])
+    reqs = np.zeros(P, polar.REQUEST_DTYPE)
+    rank = np.zeros(P, np.int64)
+    seen = [0] * len(nk)
+    for i, c in enumerate(cid):
+        rank[i] = seen[c]
+        seen[c] += 1
+    reqs["code_id"] = cid
+    reqs["llr_off"] = (np.array(bases)[cid] + rank * np.array([N for N, K in nk])[cid]) * 4
+    reqs["out_off"] = obase[cid] + rank * np.array(orow)[cid]
+    out_buf = torch.zeros(int(obase[-1]), dtype=torch.uint8, device="cuda")
+    want = torch.cat([x.reshape(-1) for x in infos])
+    bshape, bsrc = autotune.batch_shape("f32")
+    batch = polar.polar_batch_create(codes, False, bshape["threads"], bshape["smem_stage_max"],
+                                     bshape["warp_stage_max"], bshape["ctas_per_sm"])
+    budget = 4 << 30
+    arms = {"served": dict(flags=0, slots=4, max_frames=4096),
+            "plain": dict(flags=polar.SERVE_LAUNCH_PER_CODE, slots=1, max_frames=4096)}
+    mean_coded = float(np.mean([N for N, K in nk]))
+    mean_info = float(np.mean([K for N, K in nk]))
+    gate = {}
+    for name, a in arms.items():
+        out_buf.zero_()
+        serve_run(polar, batch, reqs, flat, out_buf, 2e6, P, a["flags"], a["slots"], budget,
+                  a["max_frames"], seed=1)
+        torch.cuda.synchronize()
+        gate[name] = out_buf.clone()
+    row_err = 0
+    for c in range(len(nk)):
+        got = gate["served"][int(obase[c]): int(obase[c + 1])].view(counts[c], orow[c])
+        row_err += int((got != infos[c]).any(dim=1).sum())
+    rows = []
+    with ClockSampler(0, interval_ms=1000) as clk:
+        for load in loads:
+            rate = load * 1e9 / mean_coded
+            n_total = int(min(max_frames, max(1000, rate * seconds)))
+            row = {"offered_coded_gbps": load, "frames": n_total}
+            for name, a in arms.items():
+                lat, wall, adm, launches = serve_run(
+                    polar, batch, reqs, flat, out_buf, rate, n_total, a["flags"], a["slots"],
+                    budget, a["max_frames"], seed=int(load * 7) + 11)
+                us = lat * 1e-3
+                row[name] = {"p50_us": float(np.percentile(us, 50)),
+                             "p99_us": float(np.percentile(us, 99)),
+                             "p999_us": float(np.percentile(us, 99.9)),
+                             "info_gbps": n_total * mean_info / wall / 1e9,
+                             "admissions": adm, "launches": launches}
+            rows.append(row)
+    return {
+        "what": "served (continuous batching, 4 launch slots) vs plain (one launch per code, "
+                "one batch at a time); latency = completion seen by the serving thread minus "
+                "scheduled Poisson arrival",
+        "pool": f"{P} float32 frames of the mixed codes in HBM, Eb/N0 uniform in [2.0, 4.5] dB "
+                "per frame (library device chain, seeded)",
+        "loads": rows, "bits_agree": bool(torch.equal(gate["served"], gate["plain"])),
+        "frame_errors_in_pool": row_err, "pool_frames": P,
+        "batch_shape": dict(bshape, source=bsrc), "clocks": clk.summary(),
+    }
+
+
 # ---------------------------------------------------------------- error rates
 
 FER_POINTS = {
@@ -913,7 +1185,7 @@ def run_fer(args):
         mask = synth.frozen_mask(N, K, wl["design_db"])
         for dtype in ("f32", "i8"):
             code = polar.polar_code_create(N, K, mask)
-            shape, _ = tuned_or(N, K, mask, dtype, {})
+            shape, _ = tuned_or(N, K, mask, dtype)
             shape.setdefault("stage_channel", 2)
             compile_shape(code, dtype, shape, batch)
             polar.polar_fer_run(code, dtype == "i8", points[0], 0, batch, batch)  # warm-up

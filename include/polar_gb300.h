@@ -168,8 +168,11 @@ size_t polar_code_trace_len(const polar_code_t *code);
  * into chunks of chunk_frames (0 = n_frames / 8) that move through six
  * internal streams, so copies in and out overlap decoding; the paper's latency
  * likewise counts the copies into and out of decoder memory (Sec. III). Pinned
- * host memory (cudaMallocHost) is needed for the overlap. Blocking: returns
- * when host_bits is complete; POLAR_ETIMEOUT as polar_code_check. */
+ * host memory (cudaMallocHost) is needed for the overlap. The device buffers of
+ * the chunks in flight belong to the library and are kept between calls (they
+ * grow to the largest chunk seen and are held until exit); calls on one device
+ * run one after another. Blocking: returns when host_bits is complete;
+ * POLAR_ETIMEOUT as polar_code_check. */
 polar_status polar_decode_host(const polar_code_t *code, int is_i8, const void *host_llr,
                                uint8_t *host_bits, size_t n_frames, size_t chunk_frames);
 

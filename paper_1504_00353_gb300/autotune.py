@@ -436,3 +436,64 @@ def main(argv=None):
 
 if __name__ == "__main__":
     main()
+
+
+# ---------------------------------------------------------------- shapes in use
+
+# Launch shapes used when the table holds no entry for a code on this device
+# (chosen by measurement on GB300): threads per CTA, largest shared-memory alpha
+# stage, warp-run threshold, channel read in place (stage_channel 2).
+FALLBACK = {
+    (32768, 29492, "f32"): dict(threads=128, smem_stage_max=2048, warp_stage_max=2048,
+                                stage_channel=2),
+    (32768, 29492, "i8"): dict(threads=32, smem_stage_max=512, stage_channel=2),
+    (1024, 512, "f32"): dict(threads=32, stage_channel=2),
+    (1024, 512, "i8"): dict(threads=32, stage_channel=2),
+}
+# Batch-1 (latency) shapes: one CTA, every stage in shared memory.
+FALLBACK_LATENCY = {(32768, 29492): dict(threads=256, warp_stage_max=1024)}
+COMPILE_FORM = {"auto": 0, "subtrees": 1, "memory": 2, "compact": 3, "full": 4}
+
+
+def shape_for(N: int, K: int, mask, dtype: str, latency: bool = False, default=None):
+    """The launch shape a decode of this code uses: the table's entry for this
+    device (batch-1 entry with latency=True), else the measured fallback, else
+    `default` (or the library's own choice). Returns (shape dict, source)."""
+    try:
+        e = lookup(N, K, mask, dtype, latency=latency)
+    except Exception:  # no table, or no device to name
+        e = None
+    if e:
+        return {k: e[k] for k in SHAPE_KEYS if k in e}, "tuned"
+    fb = FALLBACK_LATENCY.get((N, K)) if latency else FALLBACK.get((N, K, dtype))
+    if fb is None:
+        fb = default or {}
+    return dict(fb), "default"
+
+
+def configure(code, dtype: str, shape: dict, n_frames: int, interpreter: bool = False,
+              form: str = "auto"):
+    """Set a launch shape (polar_code_set_launch arguments plus reg_subtree and
+    frames_per_cta) on a code and compile its specialised decoder for decodes of
+    n_frames frames (unless timing the interpreter)."""
+    sh = dict(shape)
+    reg = sh.pop("reg_subtree", 0)
+    fpc = sh.pop("frames_per_cta", 1)
+    polar.polar_code_set_launch(code, dtype == "i8", **sh)
+    polar.polar_code_set_frames_per_cta(code, dtype == "i8", fpc)
+    if not interpreter:
+        polar.polar_code_compile(code, dtype == "i8", n_frames, reg, COMPILE_FORM[form])
+
+
+def batch_shape(dtype: str):
+    """Shape of the mixed-batch decoder over the mixed code set: the table's
+    entry for this device, else one warp per frame with the library's per-code
+    choices. Returns (dict of polar_batch_create arguments, source)."""
+    try:
+        e = load_table().get(device_name(), {}).get(f"mixed_{dtype}")
+    except Exception:
+        e = None
+    if e:
+        return dict(threads=e["threads"], smem_stage_max=e["smem_stage_max"],
+                    warp_stage_max=e["warp_stage_max"], ctas_per_sm=e.get("ctas_per_sm", 0)), "tuned"
+    return dict(threads=32, smem_stage_max=None, warp_stage_max=None, ctas_per_sm=0), "default"

@@ -2,8 +2,9 @@
 // in host buffers out, with the copies overlapped with decoding. The frames are
 // cut into chunks; chunk c goes to one of kDepth internal streams (copy in,
 // decode, copy out), so while one chunk decodes the next is copied in and the
-// previous one copied out. Device buffers for the chunks in flight come from
-// the library's stream-ordered pool (cached between calls).
+// previous one copied out. The device buffers for the chunks in flight belong
+// to the device and are kept between calls (they only grow), so a call does no
+// allocation once the buffers are large enough; calls on one device take turns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,24 +18,56 @@ namespace {
 
 constexpr int kDepth = 6;  // chunks in flight: buffers are reused only beyond this
 
-struct HostIoStreams {
+// Per device: kDepth non-blocking streams and one device buffer pair per
+// stream, created on first use and kept; `mu` is held for a whole call.
+struct HostIo {
+    std::mutex mu;
     cudaStream_t s[kDepth] = {};
     bool ok = false;
+    void *in[kDepth] = {};
+    uint8_t *out[kDepth] = {};
+    size_t in_cap = 0, out_cap = 0;  // bytes of each in[k] / out[k]
 };
 
-// kDepth non-blocking streams per device, created on first use and kept.
-const HostIoStreams &streams_for(int device) {
-    static std::mutex mu;
-    static std::vector<HostIoStreams> per(polar::kMaxDevices);
-    std::lock_guard<std::mutex> g(mu);
-    HostIoStreams &h = per[static_cast<size_t>(device)];
+HostIo &hostio_for(int device) {
+    static std::vector<HostIo> per(polar::kMaxDevices);
+    return per[static_cast<size_t>(device)];
+}
+
+// Make every buffer hold at least in_bytes / out_bytes (caller holds h.mu).
+cudaError_t ensure_buffers(HostIo &h, size_t in_bytes, size_t out_bytes) {
     if (!h.ok) {
         bool ok = true;
         for (int k = 0; k < kDepth && ok; ++k)
             ok = cudaStreamCreateWithFlags(&h.s[k], cudaStreamNonBlocking) == cudaSuccess;
-        h.ok = ok;
+        if (!ok) return cudaErrorUnknown;
+        h.ok = true;
     }
-    return h;
+    if (in_bytes > h.in_cap) {
+        for (int k = 0; k < kDepth; ++k) {
+            if (h.in[k]) cudaFree(h.in[k]);
+            h.in[k] = nullptr;
+        }
+        h.in_cap = 0;
+        for (int k = 0; k < kDepth; ++k) {
+            const cudaError_t e = cudaMalloc(&h.in[k], in_bytes);
+            if (e != cudaSuccess) return e;
+        }
+        h.in_cap = in_bytes;
+    }
+    if (out_bytes > h.out_cap) {
+        for (int k = 0; k < kDepth; ++k) {
+            if (h.out[k]) cudaFree(h.out[k]);
+            h.out[k] = nullptr;
+        }
+        h.out_cap = 0;
+        for (int k = 0; k < kDepth; ++k) {
+            const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&h.out[k]), out_bytes);
+            if (e != cudaSuccess) return e;
+        }
+        h.out_cap = out_bytes;
+    }
+    return cudaSuccess;
 }
 
 polar_status status_of(cudaError_t e) {
@@ -58,46 +91,35 @@ polar_status polar_decode_host(const polar_code_t *code, int is_i8, const void *
         cudaGetLastError();
         return POLAR_ECUDA;
     }
-    const HostIoStreams &hs = streams_for(device);
-    if (!hs.ok) return POLAR_ECUDA;
     const size_t es = is_i8 ? 1 : 4, in_row = size_t(code->N) * es, out_row = (code->K + 7) / 8;
     if (chunk_frames == 0) chunk_frames = std::max<size_t>(1, (n_frames + 7) / 8);
     chunk_frames = std::min(chunk_frames, n_frames);
     const size_t n_chunks = (n_frames + chunk_frames - 1) / chunk_frames;
     const int depth = static_cast<int>(std::min<size_t>(kDepth, n_chunks));
 
-    // one device buffer pair per stream, reused by every chunk on that stream
-    void *d_in[kDepth] = {};
-    uint8_t *d_out[kDepth] = {};
-    polar_status st = POLAR_OK;
-    for (int k = 0; k < depth && st == POLAR_OK; ++k) {
-        st = status_of(polar::pool_alloc(&d_in[k], chunk_frames * in_row, device, hs.s[k]));
-        if (st == POLAR_OK && out_row)
-            st = status_of(polar::pool_alloc(reinterpret_cast<void **>(&d_out[k]),
-                                             chunk_frames * out_row, device, hs.s[k]));
-    }
+    HostIo &hs = hostio_for(device);
+    std::lock_guard<std::mutex> g(hs.mu);
+    polar_status st = status_of(ensure_buffers(hs, chunk_frames * in_row, chunk_frames * out_row));
     const unsigned char *src = static_cast<const unsigned char *>(host_llr);
     for (size_t c = 0; c < n_chunks && st == POLAR_OK; ++c) {
         const int k = static_cast<int>(c % depth);
         cudaStream_t s = hs.s[k];
         const size_t f0 = c * chunk_frames, n = std::min(chunk_frames, n_frames - f0);
-        st = status_of(cudaMemcpyAsync(d_in[k], src + f0 * in_row, n * in_row,
+        st = status_of(cudaMemcpyAsync(hs.in[k], src + f0 * in_row, n * in_row,
                                        cudaMemcpyHostToDevice, s));
         if (st != POLAR_OK) break;
         const polar_stream_t ps = reinterpret_cast<polar_stream_t>(s);
-        st = is_i8 ? polar_decode_i8(code, static_cast<const int8_t *>(d_in[k]), d_out[k], n, ps)
-                   : polar_decode(code, static_cast<const float *>(d_in[k]), d_out[k], n, ps);
+        st = is_i8 ? polar_decode_i8(code, static_cast<const int8_t *>(hs.in[k]), hs.out[k], n, ps)
+                   : polar_decode(code, static_cast<const float *>(hs.in[k]), hs.out[k], n, ps);
         if (st == POLAR_OK && out_row)
-            st = status_of(cudaMemcpyAsync(host_bits + f0 * out_row, d_out[k], n * out_row,
+            st = status_of(cudaMemcpyAsync(host_bits + f0 * out_row, hs.out[k], n * out_row,
                                            cudaMemcpyDeviceToHost, s));
     }
-    for (int k = 0; k < depth; ++k) {
-        if (d_in[k]) cudaFreeAsync(d_in[k], hs.s[k]);
-        if (d_out[k]) cudaFreeAsync(d_out[k], hs.s[k]);
-    }
-    for (int k = 0; k < depth; ++k) {
-        const cudaError_t e = cudaStreamSynchronize(hs.s[k]);
-        if (st == POLAR_OK) st = status_of(e);
+    if (hs.ok) {
+        for (int k = 0; k < depth; ++k) {
+            const cudaError_t e = cudaStreamSynchronize(hs.s[k]);
+            if (st == POLAR_OK) st = status_of(e);
+        }
     }
     if (st == POLAR_OK) st = polar_code_check(const_cast<polar_code_t *>(code), nullptr);
     return st;

@@ -14,7 +14,7 @@ from paper_1504_00353_gb300 import polar, synth
 
 pytestmark = pytest.mark.gpu
 
-CODES = [(256, 128), (1024, 512), (2048, 1723), (16384, 14746)]
+CODES = [(256, 128), (1024, 512), (2048, 1723), (16384, 14746), (32768, 29492)]
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +79,7 @@ def test_served_bits_match_oracle(setup, budget_frames, slots, max_frames, shuff
     n = 400
     reqs, host_llr, host_out, llrs = make_requests(masks, n, 7 + budget_frames, shuffle)
     done_ns = np.zeros(n, np.uint64)
-    budget = budget_frames * 16384 * 4
+    budget = budget_frames * 32768 * 4  # frames of the longest code
     srv = polar.polar_server_create(batch, reqs, host_llr, host_out, done_ns, budget, max_frames,
                                     slots)
     t_pub = np.zeros(n, np.uint64)

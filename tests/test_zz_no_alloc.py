@@ -34,22 +34,35 @@ def _noalloc(code, llr, out, stream):
     return st
 
 
-@pytest.mark.parametrize("N,K,db,n", [(32768, 29492, 4.0, 700), (1024, 512, 2.5, 3000)])
+@pytest.mark.parametrize("N,K,db,n", [(32768, 29492, 4.0, 700), (1024, 512, 2.5, 3000),
+                                       (1 << 18, 220201, 3.5, 64)])
 def test_noalloc_equals_decode_on_consecutive_calls(N, K, db, n):
-    mask, d, llr = _cases.frames(N, K, db, n, seed=40, distinct=48)
+    """Bits equal polar_decode's on two calls in a row. For N = 2^18 the
+    launch's scratch (64 one-frame CTAs of about 0.9 MB each) is larger than the
+    static array, so the entry point runs fewer CTAs than polar_decode does."""
+    mask, d, llr = _cases.frames(N, K, db, n, seed=40, distinct=8 if N > 32768 else 48)
     code = polar.polar_code_create(N, K, mask)
-    if N == 32768:
-        # this launch shape keeps alpha stages above 2048 LLRs in device scratch
-        assert polar.polar_code_get_launch(code, False, n)["scratch_bytes"] > 0
+    launch = polar.polar_code_get_launch(code, False, n)
+    if N >= 32768:
+        # this launch shape keeps alpha stages above the shared-memory cap in device scratch
+        assert launch["scratch_bytes"] > 0
+    if N == 1 << 18:
+        assert launch["scratch_bytes"] > (32 << 20)  # the grid must shrink to fit the array
     stream = torch.cuda.current_stream()
     t = torch.from_numpy(llr).cuda()
     want = polar.polar_decode(code, t)
     torch.cuda.synchronize()
-    for _ in range(2):
-        out = torch.full_like(want, 0xA5)
+    outs = [torch.full_like(want, 0xA5) for _ in range(3)]
+    assert _noalloc(code, t, outs[0], stream) == 0  # first call on this device: set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for out in outs[1:]:
         assert _noalloc(code, t, out, stream) == 0
         torch.cuda.synchronize()
         polar.polar_code_check(code)
+    # the calls took no device memory (cudaMemGetInfo before and after)
+    assert torch.cuda.mem_get_info()[0] == free0
+    for out in outs:
         assert torch.equal(out, want)
     sample = np.arange(0, n, max(1, n // 16))
     assert np.array_equal(want.cpu().numpy()[sample], oracle.decode_batch(mask, llr, frames=sample))
