@@ -1097,22 +1097,31 @@ def serve_block(args, loads=(1, 10, 50, 200), seconds=0.5, max_frames=40_000):
     masks = [synth.frozen_mask(N, K, synth.MIXED_DESIGN_DB) for N, K in nk]
     codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
     cid = np.random.default_rng(4).integers(0, len(nk), P)
-    flat, views, infos, bases = device_mixed(torch, polar, codes, cid, "f32", seed=4,
-                                             ebn0_range=(2.0, 4.5))
+    _, views, infos, _ = device_mixed(torch, polar, codes, cid, "f32", seed=4,
+                                      ebn0_range=(2.0, 4.5))
     counts = [int((cid == c).sum()) for c in range(len(nk))]
     orow = [code.out_row for code in codes]
-    obase = np.concatenate([[0], np.cumsum([m * r for m, r in zip(counts, orow)])])
-    reqs = np.zeros(P, polar.REQUEST_DTYPE)
+    # the pool in arrival order, each request's frame right after the previous
+    # one's (as a stream of requests arrives), so that the loop moves runs of
+    # requests with one copy
+    sizes = np.array([nk[c][0] for c in cid], np.int64)
+    osz = np.array([orow[c] for c in cid], np.int64)
+    lo = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    oo = np.concatenate([[0], np.cumsum(osz)[:-1]])
+    flat = torch.empty(int(sizes.sum()), dtype=torch.float32, device="cuda")
     rank = np.zeros(P, np.int64)
     seen = [0] * len(nk)
     for i, c in enumerate(cid):
         rank[i] = seen[c]
         seen[c] += 1
+        flat[int(lo[i]): int(lo[i] + sizes[i])].copy_(views[c][rank[i]])
+    reqs = np.zeros(P, polar.REQUEST_DTYPE)
     reqs["code_id"] = cid
-    reqs["llr_off"] = (np.array(bases)[cid] + rank * np.array([N for N, K in nk])[cid]) * 4
-    reqs["out_off"] = obase[cid] + rank * np.array(orow)[cid]
-    out_buf = torch.zeros(int(obase[-1]), dtype=torch.uint8, device="cuda")
-    want = torch.cat([x.reshape(-1) for x in infos])
+    reqs["llr_off"] = lo * 4
+    reqs["out_off"] = oo
+    out_buf = torch.zeros(int(osz.sum()), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    del views
     bshape, bsrc = autotune.batch_shape("f32")
     batch = polar.polar_batch_create(codes, False, bshape["threads"], bshape["smem_stage_max"],
                                      bshape["warp_stage_max"], bshape["ctas_per_sm"])
@@ -1128,10 +1137,10 @@ def serve_block(args, loads=(1, 10, 50, 200), seconds=0.5, max_frames=40_000):
                   a["max_frames"], seed=1)
         torch.cuda.synchronize()
         gate[name] = out_buf.clone()
-    row_err = 0
-    for c in range(len(nk)):
-        got = gate["served"][int(obase[c]): int(obase[c + 1])].view(counts[c], orow[c])
-        row_err += int((got != infos[c]).any(dim=1).sum())
+    got = gate["served"].cpu().numpy()
+    info_h = [x.cpu().numpy() for x in infos]
+    row_err = sum(int(not np.array_equal(got[oo[i]: oo[i] + osz[i]], info_h[cid[i]][rank[i]]))
+                  for i in range(P))
     rows = []
     with ClockSampler(0, interval_ms=1000) as clk:
         for load in loads:

@@ -218,15 +218,61 @@ std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std
     return at;
 }
 
+// The stage (node size) an operation outside the register subtrees reads its
+// LLRs from, or 0 (Combine, Rate-0 and register operations read none).
+uint32_t mem_input_stage(const HostOp &op) {
+    if (op.flags & OPW_REG) return 0;
+    switch (op.kind) {
+    case OP_F: case OP_G: case OP_G0R: case OP_R1: case OP_REP: case OP_SPC: return 1u << op.log2n;
+    default: return 0;
+    }
+}
+
+// The stage an operation writes LLRs to, or 0: F/G/G_0R write stage N_v/2, and
+// a Repetition node in memory folds its sum in stage N_v/2.
+uint32_t mem_output_stage(const HostOp &op) {
+    if (op.flags & OPW_REG) return 0;
+    switch (op.kind) {
+    case OP_F: case OP_G: case OP_G0R: case OP_REP: return 1u << (op.log2n - 1);
+    default: return 0;
+    }
+}
+
+// L2 prefetches: for an operation that reads a stage held in device memory
+// (above S, or the channel when it is read in place), the point where its input
+// is fetched ahead of use is the start of the last register subtree before it,
+// provided no operation in between rewrites that stage (the subtree's work then
+// covers the fetch latency). Returns, per list index, the stages to prefetch
+// there.
+std::vector<std::vector<uint32_t>> plan_prefetch(const std::vector<HostOp> &ops, uint32_t N,
+                                                 uint32_t S, bool chan_global) {
+    std::vector<std::vector<uint32_t>> at(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        const uint32_t n = mem_input_stage(ops[i]);
+        if (!n || !((n == N && chan_global) || (n < N && n > S))) continue;
+        for (size_t j = i; j-- > 0;) {
+            if (mem_output_stage(ops[j]) == n) break;  // produced since: still in L2
+            if (ops[j].flags & OPW_REG_ENTER) {
+                at[j].push_back(n);
+                break;
+            }
+        }
+    }
+    return at;
+}
+
 // warp_frames: the body for several frames per CTA, one per warp (run by
 // run_warp_frames): every operation is warp-level on the warp's own frame, and
 // a CTA barrier after each register subtree keeps the warps in step.
+// chan_global: the channel LLRs are read in place from device memory.
 void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
                uint32_t R, const std::string &name, uint32_t outline = 0,
-               bool warp_frames = false) {
+               bool warp_frames = false, bool chan_global = true) {
     const bool outline_sub = outline & kOutlineSubtrees, outline_mem = outline & kOutlineMemory;
     const uint32_t N = code.N;
     const std::vector<HostOp> ops = code.build_ops(R);
+    const std::vector<std::vector<uint32_t>> prefetch = plan_prefetch(ops, N, S, chan_global);
+    const uint32_t es = is_i8 ? 1u : 4u;
     const char *T = is_i8 ? "int8_t" : "float";
     std::map<size_t, size_t> sub_at;
     if (outline_sub) sub_at = emit_subtree_functions(o, ops, T, R, name + "_");
@@ -336,6 +382,8 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             continue;
         }
         const char *align = warp_frames ? "      __syncthreads();\n" : "";
+        for (uint32_t pn : prefetch[i])
+            o << "      prefetch_l2(" << in(pn) << ", " << pn * es << "u);\n";
         if (outline_sub && (op.flags & OPW_REG_ENTER)) {  // the whole subtree is one call
             o << "      " << name << "_sub" << sub_at.at(i) << "(" << in(n) << ", fr.beta, " << op.off
               << "u);\n      __syncwarp();\n" << align;
@@ -370,7 +418,7 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
       << "namespace polar {\n";
     const bool warp_frames = shape.frames_per_cta > 1;
     emit_body(o, code, is_i8, shape.smem_stage_max, shape.warp_stage_max, reg_subtree, "GenBody",
-              outline, warp_frames);
+              outline, warp_frames, warp_frames || !shape.stage_channel);
     o << "}  // namespace polar\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << shape.threads << ", "
       << std::max<uint32_t>(shape.ctas_per_sm, 1) << ") polar_unrolled(const polar::KernelArgs a) {\n";

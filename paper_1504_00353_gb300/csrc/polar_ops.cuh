@@ -156,20 +156,21 @@ constexpr uint32_t kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------- element ops
 
+// Eq. 1: min(|a|, |b|) carrying the XOR of the two signs, one instruction.
 __device__ __forceinline__ float f_f32(float a, float b) {
-    const float m = fminf(fabsf(a), fabsf(b));
-    return __uint_as_float(__float_as_uint(m) |
-                           ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u));
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
 }
 // Eq. 2 with beta_l as the sign bit of alpha_v[i] (Listing 3): one IEEE add.
 __device__ __forceinline__ float g_f32(float a, float b, uint32_t bit) {
     return b + __uint_as_float(__float_as_uint(a) ^ (bit << 31));
 }
 __device__ __forceinline__ int sat127(int v) { return max(-127, min(127, v)); }
-__device__ __forceinline__ int f_i8s(int a, int b) {
-    const int m = min(abs(a), abs(b));
-    return (a ^ b) < 0 ? -m : m;
-}
+// Eq. 1 on integers: max(min(a, b), -max(a, b)) equals sgn(a) sgn(b) min(|a|, |b|)
+// (both positive: min(a, b); both negative: -max(a, b) = min(|a|, |b|); mixed
+// signs: the negative one of min(a, b) and -max(a, b) with the smaller magnitude).
+__device__ __forceinline__ int f_i8s(int a, int b) { return max(min(a, b), -max(a, b)); }
 __device__ __forceinline__ int g_i8s(int a, int b, uint32_t bit) {
     return sat127(bit ? b - a : b + a);
 }
@@ -188,10 +189,27 @@ __device__ __forceinline__ uint32_t mag_bits(int a) { return static_cast<uint32_
 __device__ __forceinline__ uint32_t bytes_from_bits4(uint32_t bits4) {
     return ((bits4 * 0x00204081u) & 0x01010101u) * 0xFFu;  // bit k -> byte k = 0xFF
 }
+// 0xFF in every byte of x whose sign bit is set (prmt's sign-replicating byte
+// selectors 8..B), 0x00 elsewhere.
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t x) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(x));
+    return r;
+}
+// Eq. 1 on four bytes in [-127, 127]. Per byte: |a| = (a ^ s) + (s & 1) with s
+// the sign mask (no carry leaves a byte: the sum is at most 127); |a| >= |b| is
+// bit 7 of (|a| | 0x80) - |b| (no borrow leaves a byte: the difference is at
+// least 1); the magnitude m is negated where the signs differ as
+// (0x80 - m) ^ 0x80, which maps 0 to 0 and stays inside the byte.
 __device__ __forceinline__ uint32_t f_i8x4(uint32_t a, uint32_t b) {
-    const uint32_t m = __vminu4(__vabsss4(a), __vabsss4(b));
-    const uint32_t sel = (((a ^ b) & 0x80808080u) >> 7) * 0xFFu;
-    return (m & ~sel) | (__vneg4(m) & sel);
+    const uint32_t sa = sign_bytes(a), sb = sign_bytes(b);
+    const uint32_t ma = (a ^ sa) + (sa & 0x01010101u);
+    const uint32_t mb = (b ^ sb) + (sb & 0x01010101u);
+    const uint32_t ge = sign_bytes((ma | 0x80808080u) - mb);
+    const uint32_t m = (mb & ge) | (ma & ~ge);
+    const uint32_t ns = sa ^ sb;
+    const uint32_t neg = (0x80808080u - m) ^ 0x80808080u;
+    return (neg & ns) | (m & ~ns);
 }
 __device__ __forceinline__ uint32_t g_i8x4(uint32_t a, uint32_t b, uint32_t bits4) {
     const uint32_t sel = bytes_from_bits4(bits4);
@@ -371,10 +389,53 @@ __device__ __forceinline__ void op_r0(uint32_t *beta, uint32_t n, uint32_t o) {
 
 // ---------------------------------------------------------------- node decoders in memory
 
+// Sign bits of the 16 int8 values of v, value k at bit k. Per word the sign
+// bits 7, 15, 23, 31 are moved to bits 28..31 by one multiply (the partial
+// products of 0x00204081 land on distinct bits, so nothing carries).
+__device__ __forceinline__ uint32_t sign_bits16(uint4 v) {
+    const uint32_t m0 = ((v.x & 0x80808080u) * 0x00204081u) >> 28;
+    const uint32_t m1 = ((v.y & 0x80808080u) * 0x00204081u) >> 28;
+    const uint32_t m2 = ((v.z & 0x80808080u) * 0x00204081u) >> 28;
+    const uint32_t m3 = ((v.w & 0x80808080u) * 0x00204081u) >> 28;
+    return m0 | (m1 << 4) | (m2 << 8) | (m3 << 12);
+}
+
+// Rate-1 (Eq. 4) on int8 LLRs, n >= 32: 16 values per lane per 16-byte load;
+// lanes 2j and 2j + 1 of a warp hold the two halves of one beta word. Four
+// loads per lane are in flight before the first is used.
+template <class Grp>
+__device__ __forceinline__ void op_r1_i8v(const int8_t *__restrict__ in, uint32_t *beta,
+                                          uint32_t n, uint32_t o) {
+    const uint4 *v = reinterpret_cast<const uint4 *>(in);
+    const uint32_t nv = n >> 4, lane = threadIdx.x & 31u;
+    const uint32_t w0 = Grp::kCta ? (threadIdx.x & ~31u) : 0u;
+    const uint32_t step = Grp::kCta ? blockDim.x : 32u;
+    for (uint32_t base = w0; base < nv; base += 4 * step) {
+        uint32_t m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t i = base + k * step + lane;
+            m[k] = i < nv ? sign_bits16(v[i]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t i = base + k * step + lane;
+            const uint32_t hi = __shfl_down_sync(kFull, m[k], 1);
+            if (i < nv && !(lane & 1u)) beta[(o >> 5) + (i >> 1)] = m[k] | (hi << 16);
+        }
+    }
+}
+
 // Rate-1 (Eq. 4): one ballot per 32 consecutive elements; four chunks loaded ahead.
 template <typename T, class Grp>
 __device__ __forceinline__ void op_r1(const T *__restrict__ in, uint32_t *beta, uint32_t n,
                                       uint32_t o) {
+    if constexpr (sizeof(T) == 1) {
+        if (n >= 32) {
+            op_r1_i8v<Grp>(reinterpret_cast<const int8_t *>(in), beta, n, o);
+            return;
+        }
+    }
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t w0 = Grp::kCta ? (threadIdx.x >> 5) : 0u;
     const uint32_t ws = Grp::kCta ? (blockDim.x >> 5) : 1u;
@@ -511,6 +572,19 @@ __device__ __forceinline__ void op_rep(const T *in, T *tmp, uint32_t *beta, uint
         } else if (lane == 0) {
             write_field(beta, o, n, word);
         }
+    }
+}
+
+// ---------------------------------------------------------------- L2 prefetch
+
+// Ask L2 to fetch [p, p + bytes) ahead of use (cp.async.bulk.prefetch: a hint
+// with nothing to wait for). Called by a whole warp; lane k issues the k-th
+// 4 KiB slice. p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    for (uint32_t off = (threadIdx.x & 31u) * 4096u; off < bytes; off += 32u * 4096u) {
+        const uint32_t n = bytes - off < 4096u ? bytes - off : 4096u;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                     ::"l"(static_cast<const char *>(p) + off), "r"(n) : "memory");
     }
 }
 
@@ -893,14 +967,30 @@ struct RegSub {
         }
     }
 
-    // Store the subtree's n0 bits at leaf offset o0 of beta.
+    // Store the subtree's n0 bits at leaf offset o0 of beta. The words are the
+    // same on every lane, so lane 0 stores them, 16 bytes at a time (o0 is a
+    // multiple of n0, so the words are 16-byte aligned from 128 leaves up).
     template <uint32_t n0>
     __device__ __forceinline__ void exit(uint32_t *beta, uint32_t o0) {
-        if constexpr (n0 >= 32) {
-            static_for<0, n0 / 32>([&](auto kc) {
-                constexpr uint32_t k = decltype(kc)::value;
-                if (lane == k) beta[(o0 >> 5) + k] = bw[k];
-            });
+        if constexpr (n0 >= 128) {
+            if (lane == 0) {
+                static_for<0, n0 / 128>([&](auto kc) {
+                    constexpr uint32_t k = decltype(kc)::value;
+                    uint4 q;
+                    q.x = bw[4 * k];
+                    q.y = bw[4 * k + 1];
+                    q.z = bw[4 * k + 2];
+                    q.w = bw[4 * k + 3];
+                    *reinterpret_cast<uint4 *>(beta + (o0 >> 5) + 4 * k) = q;
+                });
+            }
+        } else if constexpr (n0 >= 32) {
+            if (lane == 0) {
+                static_for<0, n0 / 32>([&](auto kc) {
+                    constexpr uint32_t k = decltype(kc)::value;
+                    beta[(o0 >> 5) + k] = bw[k];
+                });
+            }
         } else {
             if (lane == 0) write_field(beta, o0, n0, bw[0]);
         }

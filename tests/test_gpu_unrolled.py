@@ -142,20 +142,6 @@ def test_outlined_forms(i8, form):
         assert np.array_equal(decode(code, yy, i8), oracle.decode_batch(m, yy))
 
 
-def test_n1m_compact_sampled():
-    """N = 2^20, K = 880,804 (28,465 operations): the default compile picks the
-    compact form; 64 int8 frames decoded, 3 compared with the oracle."""
-    N, K = 1 << 20, 880804
-    mask, d, llr = _cases.frames(N, K, 3.5, 64, seed=36, distinct=3)
-    y = synth.quantize_i8(llr)
-    code = polar.polar_code_create(N, K, mask)
-    polar.polar_code_compile(code, True, 64)
-    assert polar.polar_code_get_launch(code, True, 64)["unrolled"] == 256
-    got = decode(code, y, True)
-    sample = np.array([0, 33, 63])
-    assert np.array_equal(got[sample], oracle.decode_batch(mask, y, frames=sample))
-
-
 def test_release_returns_to_interpreter():
     mask, d, llr = _cases.frames(256, 128, 3.0, 50, seed=32)
     code = polar.polar_code_create(256, 128, mask)
