@@ -356,25 +356,65 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
         }
     };
 
+    // Memory-resident F/G/G_0R operation i followed by up to two operations
+    // that each read the stage the previous one wrote (the first operation of
+    // the node it produced LLRs for: F or G_0R): emitted as one fused op_chain
+    // when the last stage holds at least one vector per column. Returns the
+    // number of operations covered (1 = not fused).
+    const uint32_t vec = is_i8 ? 16u : 4u;
+    auto chain_len = [&](size_t i) -> uint32_t {
+        const HostOp &a = ops[i];
+        if ((a.flags & OPW_REG) || a.kind > OP_G0R) return 1;
+        uint32_t len = 1;
+        for (size_t j = i; len < 3 && j + 1 < ops.size(); ++j, ++len) {
+            const HostOp &p = ops[j], &q = ops[j + 1];
+            const uint32_t pn = 1u << p.log2n;
+            const uint32_t child_off = p.kind == OP_F ? p.off : p.off + pn / 2;
+            if ((q.flags & OPW_REG) || (q.kind != OP_F && q.kind != OP_G0R) ||
+                q.log2n + 1 != p.log2n || q.off != child_off)
+                break;
+        }
+        while (len > 1 && ((1u << a.log2n) >> len) < vec) --len;
+        return len;
+    };
+    auto chain_op = [&](size_t i, uint32_t len, const char *grp) {
+        const HostOp &a = ops[i];
+        const uint32_t n = 1u << a.log2n;
+        o << "      " << (outline_mem ? "mem_chain" : "op_chain") << "<T, " << grp << ", " << len
+          << "u, " << kind_name(a.kind) << ", " << kind_name(ops[i + 1].kind) << ", "
+          << (len == 3 ? kind_name(ops[i + 2].kind) : "polar::OP_F") << ">(" << in(n) << ", "
+          << out(n / 2) << ", " << out(n / 4) << ", " << (len == 3 ? out(n / 8) : "nullptr")
+          << ", " << n << "u, fr.beta, " << a.off << "u);\n";
+    };
+
     bool in_run = false;
     uint32_t o0 = 0, n0 = 0;
     for (size_t i = 0; i < ops.size(); ++i) {
         const HostOp &op = ops[i];
         const uint32_t n = 1u << op.log2n;
         const bool narrow = warp_frames || n <= W || (op.flags & OPW_REG);
+        const uint32_t clen = chain_len(i);
         if (!narrow) {
             if (in_run) {
                 o << "    }\n    __syncthreads();\n";
                 in_run = false;
             }
             o << "    {\n";
-            mem_op(op, "CtaGrp");
+            if (clen > 1) chain_op(i, clen, "CtaGrp");
+            else mem_op(op, "CtaGrp");
             o << "    }\n    __syncthreads();\n";
+            i += clen - 1;
             continue;
         }
         if (!in_run) {
             o << (warp_frames ? "    {\n" : "    if (warp == 0) {\n");
             in_run = true;
+        }
+        if (!(op.flags & OPW_REG) && clen > 1) {
+            chain_op(i, clen, "WarpGrp");
+            o << "      __syncwarp();\n";
+            i += clen - 1;
+            continue;
         }
         if (!(op.flags & OPW_REG)) {
             mem_op(op, "WarpGrp");

@@ -358,6 +358,48 @@ __device__ __forceinline__ void op_fg(const T *__restrict__ in, T *__restrict__ 
     }
 }
 
+// A chain of L = 2 or 3 operations down the tree, fused: K0 on node (o, n)
+// (F, G or G_0R), then K1 and K2 (F or G_0R) on the node of the next stage
+// that the previous operation produced the LLRs of. In list order these are
+// consecutive operations, each reading the stage the one before it just
+// wrote. Here every thread loads the 2^L inputs of one column of outputs
+// (elements j + m n / 2^L of stage n) once, keeps the intermediate values in
+// registers and stores each intermediate stage as well (a later operation
+// reads it again) and the last one. Element by element this is the same
+// arithmetic as the L operations one after another. stage1/2/3 = stages n/2,
+// n/4, n/8; (n >> L) must be a multiple of the vector width.
+template <typename T, class Grp, uint32_t L, uint32_t K0, uint32_t K1, uint32_t K2>
+__device__ __forceinline__ void op_chain(const T *__restrict__ in, T *__restrict__ stage1,
+                                         T *__restrict__ stage2, T *__restrict__ stage3,
+                                         uint32_t n, const uint32_t *beta, uint32_t o) {
+    using Vec = typename Llr<T>::Vec;
+    constexpr uint32_t V = Llr<T>::V, M = 1u << L;
+    const uint32_t nvc = (n >> L) / V;  // vector columns of the last stage
+    const Vec *vi = reinterpret_cast<const Vec *>(in);
+    Vec *v1 = reinterpret_cast<Vec *>(stage1);
+    Vec *v2 = reinterpret_cast<Vec *>(stage2);
+    Vec *v3 = reinterpret_cast<Vec *>(stage3);
+    for (uint32_t c = Grp::rank(); c < nvc; c += Grp::size()) {
+        Vec x[M];
+#pragma unroll
+        for (uint32_t m = 0; m < M; ++m) x[m] = vi[c + m * nvc];
+        Vec y[M / 2];
+#pragma unroll
+        for (uint32_t m = 0; m < M / 2; ++m) {
+            const uint32_t bits = K0 == OP_G ? bits_at(beta, o + (c + m * nvc) * V, V) : 0u;
+            y[m] = fg4<K0>(x[m], x[m + M / 2], bits);
+            v1[c + m * nvc] = y[m];
+        }
+        Vec z[M / 4];
+#pragma unroll
+        for (uint32_t m = 0; m < M / 4; ++m) {
+            z[m] = fg4<K1>(y[m], y[m + M / 4], 0u);
+            v2[c + m * nvc] = z[m];
+        }
+        if constexpr (L == 3) v3[c] = fg4<K2>(z[0], z[1], 0u);
+    }
+}
+
 // ---------------------------------------------------------------- Combine / Rate-0 in memory
 
 template <class Grp>
@@ -839,6 +881,11 @@ template <typename T, class Grp, uint32_t KIND>
 __device__ __noinline__ void mem_fg(const T *in, T *out, uint32_t h, const uint32_t *beta,
                                     uint32_t o) {
     op_fg<T, Grp, KIND>(in, out, h, beta, o);
+}
+template <typename T, class Grp, uint32_t L, uint32_t K0, uint32_t K1, uint32_t K2>
+__device__ __noinline__ void mem_chain(const T *in, T *stage1, T *stage2, T *stage3, uint32_t n,
+                                       const uint32_t *beta, uint32_t o) {
+    op_chain<T, Grp, L, K0, K1, K2>(in, stage1, stage2, stage3, n, beta, o);
 }
 template <class Grp>
 __device__ __noinline__ void mem_combine(uint32_t *beta, uint32_t n, uint32_t o, bool copy) {
