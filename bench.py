@@ -66,7 +66,8 @@ def parse():
                    default="auto",
                    help="form of the specialised decoder: what is compiled out of line (auto: "
                         "compact above 4096 operations, else the tuned form)")
-    p.add_argument("--mode", choices=["throughput", "mixed", "serve", "fer"], default="throughput",
+    p.add_argument("--mode", choices=["throughput", "mixed", "serve", "fer", "latency"],
+                   default="throughput",
                    help="throughput: one code, batch and batch-1 (default); mixed: 65,536 frames "
                         "of five codes, one persistent launch in a CUDA graph vs one launch per "
                         "code; serve: Poisson arrivals through the serving loop vs a plain queue; "
@@ -397,6 +398,49 @@ def device_timed(torch, stream, fn, steps, warmup, world):
     return max_over_ranks(world, t0.elapsed_time(t1)), statistics.mean(a.elapsed_time(b) for a, b in ev)
 
 
+def latency_block(torch, polar, args, N, K, mask, dtype, frames_dev, frames_host, nlat):
+    """Batch-1 decodes of nlat frames with the decoder specialised for single
+    frames: device time (the launch queued behind a spin so host call overhead
+    is not counted) and end to end (copy in from pinned host memory, decode, copy
+    out, host clock)."""
+    i8 = dtype == "i8"
+    row = (K + 7) // 8
+    stream = torch.cuda.current_stream()
+    decode = polar.polar_decode_i8 if i8 else polar.polar_decode
+    lcode = polar.polar_code_create(N, K, mask)
+    lshape, _ = tuned_or(N, K, mask, dtype, latency=True)
+    compile_shape(lcode, dtype, lshape, 1, args.interpreter, args.compile_form)
+    one_in = torch.empty((1, N), dtype=frames_dev.dtype, device="cuda")
+    one_out = torch.empty((1, row), dtype=torch.uint8, device="cuda")
+    h1 = torch.empty((1, row), dtype=torch.uint8).pin_memory()
+    lat_dev, lat_e2e = [], []
+    n = frames_dev.shape[0]
+    for f in range(nlat + 5):
+        one_in.copy_(frames_dev[f % n: f % n + 1])
+        torch.cuda.synchronize()
+        torch.cuda._sleep(1_000_000)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        decode(lcode, one_in, one_out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_in.copy_(frames_host[f % n: f % n + 1], non_blocking=True)
+        decode(lcode, one_in, one_out)
+        h1.copy_(one_out, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if f >= 5:
+            lat_dev.append(a.elapsed_time(b) * 1e3)
+            lat_e2e.append((t1 - t0) * 1e6)
+    return {"batch": 1, "frames": nlat,
+            "device_p50": float(np.percentile(lat_dev, 50)),
+            "device_p99": float(np.percentile(lat_dev, 99)),
+            "e2e_p50": float(np.percentile(lat_e2e, 50)),
+            "e2e_p99": float(np.percentile(lat_e2e, 99)),
+            "launch": polar.polar_code_get_launch(lcode, i8, 1), "shape": lshape}
+
+
 def run_native(args, world, rank, local):
     import torch
 
@@ -484,44 +528,12 @@ def run_native(args, world, rank, local):
         torch.cuda.synchronize()
         assert np.array_equal(host_out.numpy(), out.cpu().numpy()), "host-buffer decode differs"
 
-    # batch-1 frame latency, with the decoder specialised for single frames:
-    # device time (the launch queued behind a spin so host overhead is not
-    # counted) and end to end (copy in, decode, copy out, host clock)
+    # batch-1 frame latency, with the decoder specialised for single frames
     lat = None
     nlat = min(args.latency_frames, batch)
     if nlat:
-        i8 = main == "i8"
-        lcode = polar.polar_code_create(N, K, mask)
-        lshape, _ = tuned_or(N, K, mask, main, latency=True)
-        compile_shape(lcode, main, lshape, 1, args.interpreter, args.compile_form)
-        one_in = torch.empty((1, N), dtype=r["bufs"][0].dtype, device=dev)
-        one_out = torch.empty((1, row), dtype=torch.uint8, device=dev)
-        h1 = torch.empty((1, row), dtype=torch.uint8).pin_memory()
-        lat_dev, lat_e2e = [], []
-        for f in range(nlat + 5):
-            one_in.copy_(r["bufs"][0][f % batch: f % batch + 1])
-            torch.cuda.synchronize()
-            torch.cuda._sleep(1_000_000)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            decode(lcode, one_in, one_out)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            one_in.copy_(host_in[f % batch: f % batch + 1], non_blocking=True)
-            decode(lcode, one_in, one_out)
-            h1.copy_(one_out, non_blocking=True)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            if f >= 5:
-                lat_dev.append(a.elapsed_time(b) * 1e3)
-                lat_e2e.append((t1 - t0) * 1e6)
-        lat = {"batch": 1, "frames": nlat,
-               "device_p50": float(np.percentile(lat_dev, 50)),
-               "device_p99": float(np.percentile(lat_dev, 99)),
-               "e2e_p50": float(np.percentile(lat_e2e, 50)),
-               "e2e_p99": float(np.percentile(lat_e2e, 99)),
-               "launch": polar.polar_code_get_launch(lcode, i8, 1)}
+        lat = latency_block(torch, polar, args, N, K, mask, main, r["bufs"][0][:nlat], host_in[:nlat],
+                            nlat)
 
     hbm_peak, peak_kind = peaks()
     es = 1 if main == "i8" else 4
@@ -656,135 +668,39 @@ def batch_shape(dtype):
 
 
 def run_mixed(args):
-    """65,536 frames drawn uniformly from five codes, int8 LLRs: one persistent
-    launch of the mixed-batch decoder replayed from a CUDA graph, against one
-    launch per code (each code's frames contiguous, its own tuned decoder)."""
+    """Config 3 on its own line: the mixed-length batch block of the default
+    line (65,536 int8 frames of five codes, one persistent launch replayed from
+    a CUDA graph against one launch per code)."""
+    import torch
+    torch.cuda.set_device(0)
+    blk = mixed_block(args, n=args.batch or None, steps=args.steps, warmup=args.warmup)
+    line = {"metric": "info-bit Gbps, mixed-length batch", "mode": "mixed",
+            "value": blk["batched"]["gbps"], "unit": "Gbps", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": blk["batched"]["step_ms"],
+            "higher_is_better": True, "dtype": "i8", "data": "synthetic",
+            "config": {"workload": f"mixed{blk['frames']}", "codes": blk["codes"]},
+            "gpu_launches": args.steps, **{k: v for k, v in blk.items() if k != "codes"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_latency(args):
+    """Batch-1 latency of the workload's code on its own line (the latency
+    block of the default line): the decoder specialised for single frames."""
     import torch
 
     from paper_1504_00353_gb300 import polar
-    dtype = args.dtype
-    n = args.batch or synth.MIXED_FRAMES
     torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream(dev)
-    nk = synth.MIXED_CODES
-    t_gen = time.perf_counter()
-    masks, cid, llr, bits = mixed_inputs(n, dtype, seed=3)
-    t_gen = time.perf_counter() - t_gen
-    es = 1 if dtype == "i8" else 4
-    info_bits = sum(int((cid == c).sum()) * K for c, (N, K) in enumerate(nk))
-
-    # plain: one launch per code over that code's frames
-    codes, outs, bufs, shapes = [], [], [], []
-    for c, (N, K) in enumerate(nk):
-        shape, src = tuned_or(N, K, masks[c], dtype,
-                              default=dict(threads=32, smem_stage_max=512, warp_stage_max=2048,
-                                           ctas_per_sm=0))
-        shape.setdefault("stage_channel", 2)
-        code = polar.polar_code_create(N, K, masks[c])
-        compile_shape(code, dtype, shape, llr[c].shape[0])
-        codes.append(code)
-        shapes.append(dict(shape, source=src))
-        bufs.append(torch.from_numpy(llr[c]).to(dev))
-        outs.append(torch.empty((llr[c].shape[0], (K + 7) // 8), dtype=torch.uint8, device=dev))
-    dec = polar.polar_decode_i8 if dtype == "i8" else polar.polar_decode
-
-    def plain(_):
-        for c in range(len(nk)):
-            dec(codes[c], bufs[c], outs[c])
-
-    # batched: frames in arrival order in one buffer, descriptors longest first
-    order = np.lexsort((np.arange(n), -np.array([nk[c][0] for c in cid])))
-    sizes = np.array([nk[c][0] for c in cid], np.int64)
-    orow = np.array([(nk[c][1] + 7) // 8 for c in cid], np.int64)
-    lo = np.concatenate([[0], np.cumsum(sizes)[:-1]])
-    oo = np.concatenate([[0], np.cumsum(orow)[:-1]])
-    flat = np.empty(int(sizes.sum()), llr[0].dtype)
-    pos = [0] * len(nk)
-    for i in range(n):  # arrival layout
-        c = cid[i]
-        flat[lo[i]: lo[i] + sizes[i]] = llr[c][pos[c]]
-        pos[c] += 1
-    d_flat = torch.from_numpy(flat).to(dev)
-    d_ids = torch.from_numpy(cid[order].astype(np.int32)).to(dev)
-    d_lo = torch.from_numpy(lo[order].astype(np.int64)).to(dev)
-    d_oo = torch.from_numpy(oo[order].astype(np.int64)).to(dev)
-    d_out = torch.zeros(int(orow.sum()), dtype=torch.uint8, device=dev)
-    bshape, bsrc = batch_shape(dtype)
-    t_c = time.perf_counter()
-    batch = polar.polar_batch_create(codes, dtype == "i8", bshape["threads"],
-                                     bshape["smem_stage_max"], bshape["warp_stage_max"],
-                                     bshape["ctas_per_sm"])
-    t_c = time.perf_counter() - t_c
-    binfo = polar.polar_batch_info(batch)
-    s2 = torch.cuda.Stream(dev)
-    s2.wait_stream(stream)
-    with torch.cuda.stream(s2):
-        polar.polar_batch_decode(batch, d_ids, d_lo, d_oo, d_flat, d_out, stream=s2)
-    stream.wait_stream(s2)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        polar.polar_batch_decode(batch, d_ids, d_lo, d_oo, d_flat, d_out)
-    torch.cuda.synchronize()
-
-    # the two forms must agree bit for bit (both are the product path), and match
-    # the transmitted bits except for frame errors
-    plain(0)
-    graph.replay()
-    torch.cuda.synchronize()
-    got = d_out.cpu().numpy()
-    pos = [0] * len(nk)
-    agree, ferr = True, 0
-    for i in range(n):
-        c = cid[i]
-        a = got[oo[i]: oo[i] + orow[i]]
-        b = outs[c][pos[c]].cpu().numpy() if i < 64 else None
-        if b is not None and not np.array_equal(a, b):
-            agree = False
-        ferr += int(not np.array_equal(a, bits[c][pos[c]]))
-        pos[c] += 1
-    host_plain = [o.cpu().numpy() for o in outs]
-    pos = [0] * len(nk)
-    for i in range(n):
-        c = cid[i]
-        agree &= bool(np.array_equal(got[oo[i]: oo[i] + orow[i]], host_plain[c][pos[c]]))
-        pos[c] += 1
-
-    with ClockSampler(0) as clk:
-        plain_ms, _ = device_timed(torch, stream, plain, args.steps, args.warmup, 1)
-        batched_ms, _ = device_timed(torch, stream, lambda i: graph.replay(), args.steps,
-                                     args.warmup, 1)
-    per_code_ms = []
-    for c in range(len(nk)):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(3):
-            dec(codes[c], bufs[c], outs[c])
-        b.record(stream)
-        torch.cuda.synchronize()
-        per_code_ms.append(a.elapsed_time(b) / 3)
-    line = {
-        "metric": "info-bit Gbps, mixed-length batch", "mode": "mixed",
-        "value": info_bits * args.steps / (batched_ms * 1e-3) / 1e9, "unit": "Gbps",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": batched_ms / args.steps, "higher_is_better": True, "dtype": dtype,
-        "data": "synthetic",
-        "config": {"workload": f"mixed{n}", "codes": nk, "design_db": synth.MIXED_DESIGN_DB,
-                   "frames": n, "frames_per_code": [int((cid == c).sum()) for c in range(len(nk))],
-                   "llr": dtype, "l2": f"inputs {flat.nbytes / 2**20:.0f} MiB, larger than L2"},
-        "batched": {"gbps": info_bits * args.steps / (batched_ms * 1e-3) / 1e9,
-                    "step_ms": batched_ms / args.steps, "launches_per_step": 1,
-                    "cuda_graph": True, "shape": dict(bshape, source=bsrc), "launch": binfo,
-                    "compile_s": t_c},
-        "plain": {"gbps": info_bits * args.steps / (plain_ms * 1e-3) / 1e9,
-                  "step_ms": plain_ms / args.steps, "launches_per_step": len(nk),
-                  "per_code_ms": per_code_ms, "shapes": shapes},
-        "batched_over_plain": plain_ms / batched_ms,
-        "bits_agree": agree, "frame_errors": ferr, "input_gen_s": t_gen,
-        "gpu_launches": args.steps, "clocks": clk.summary(),
-    }
-    print(json.dumps(line), flush=True)
+    wl = dict(synth.WORKLOADS[args.workload])
+    N, K = wl["N"], wl["K"]
+    nlat = args.latency_frames
+    mask, _, d, llr32 = make_inputs(wl, nlat, wl["seed"], "f32")
+    y = synth.quantize_i8(llr32) if args.dtype == "i8" else llr32
+    lat = latency_block(torch, polar, args, N, K, mask, args.dtype, torch.from_numpy(y).cuda(),
+                        torch.from_numpy(y).pin_memory(), nlat)
+    print(json.dumps({"metric": "batch-1 frame latency", "mode": "latency", "unit": "us",
+                      "value": lat["device_p50"], "higher_is_better": False, "dtype": args.dtype,
+                      "data": "synthetic", "config": {"workload": args.workload, "N": N, "K": K},
+                      "latency_us": lat}), flush=True)
 
 
 # ---------------------------------------------------------------- serving
@@ -1224,6 +1140,8 @@ def main():
         return run_mixed(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "latency":
+        return run_latency(args)
     if args.impl == "reference":
         # the CPU oracle arm: rank 0 alone runs and prints, other ranks exit
         if int(os.environ.get("RANK", "0")) == 0:

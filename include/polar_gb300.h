@@ -258,11 +258,16 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
  * patterns share code); POLAR_COMPILE_OUTLINE_MEMORY calls memory-resident
  * operations out of line with run-time sizes; POLAR_COMPILE_COMPACT is both
  * (N = 2^20 codes, 28,465 operations, compile in about a minute);
- * POLAR_COMPILE_FULL forces the full form. Results are the same bits. */
+ * POLAR_COMPILE_FULL forces the full form. POLAR_COMPILE_LOCAL_LEAVES (combinable
+ * with any of these) decodes every split node of 4 to 16 leaves inside a
+ * register subtree with each thread of the warp holding the whole node,
+ * without shuffles: fewer dependent steps, more instructions, so it suits
+ * single-frame (latency) shapes. Results are the same bits. */
 #define POLAR_COMPILE_OUTLINE_SUBTREES 1u
 #define POLAR_COMPILE_OUTLINE_MEMORY 2u
 #define POLAR_COMPILE_COMPACT 3u
 #define POLAR_COMPILE_FULL 4u
+#define POLAR_COMPILE_LOCAL_LEAVES 8u
 polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frames,
                                    uint32_t reg_subtree, uint32_t flags);
 

@@ -103,8 +103,9 @@ def frames_for(N: int, sms: int) -> int:
 
 
 SHAPE_KEYS = ("threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm", "stage_channel",
-              "reg_subtree", "frames_per_cta")
-SHAPE_DEFAULTS = dict(ctas_per_sm=0, stage_channel=2, reg_subtree=256, frames_per_cta=1)
+              "reg_subtree", "frames_per_cta", "local_leaves")
+SHAPE_DEFAULTS = dict(ctas_per_sm=0, stage_channel=2, reg_subtree=256, frames_per_cta=1,
+                      local_leaves=0)
 
 
 def _shape_key(s: dict) -> tuple:
@@ -123,7 +124,8 @@ def apply_shape(code, dtype: str, shape: dict, n_frames: int):
                                 warp_stage_max=sh["warp_stage_max"],
                                 ctas_per_sm=sh["ctas_per_sm"], stage_channel=sh["stage_channel"])
     polar.polar_code_set_frames_per_cta(code, dtype == "i8", sh["frames_per_cta"])
-    polar.polar_code_compile(code, dtype == "i8", n_frames, sh["reg_subtree"])
+    polar.polar_code_compile(code, dtype == "i8", n_frames, sh["reg_subtree"],
+                             polar.COMPILE_LOCAL_LEAVES if sh["local_leaves"] else 0)
 
 
 def _compile(N, K, mask, dtype, shape, n_frames):
@@ -251,6 +253,8 @@ class CodeTuner:
         self.measure([dict(cur, reg_subtree=r) for r in (256, 512, 1024)])
         cur, _ = self.best()
         self.measure([dict(cur, stage_channel=c) for c in (1, 2)])
+        cur, _ = self.best()
+        self.measure([dict(cur, local_leaves=v) for v in (0, 1)])
         return self.best()
 
     def tune(self, threads_options=THREADS, fixed_threads=None, tune_ctas=True) -> tuple[dict, float]:
@@ -479,10 +483,11 @@ def configure(code, dtype: str, shape: dict, n_frames: int, interpreter: bool = 
     sh = dict(shape)
     reg = sh.pop("reg_subtree", 0)
     fpc = sh.pop("frames_per_cta", 1)
+    local = polar.COMPILE_LOCAL_LEAVES if sh.pop("local_leaves", 0) else 0
     polar.polar_code_set_launch(code, dtype == "i8", **sh)
     polar.polar_code_set_frames_per_cta(code, dtype == "i8", fpc)
     if not interpreter:
-        polar.polar_code_compile(code, dtype == "i8", n_frames, reg, COMPILE_FORM[form])
+        polar.polar_code_compile(code, dtype == "i8", n_frames, reg, COMPILE_FORM[form] | local)
 
 
 def batch_shape(dtype: str):

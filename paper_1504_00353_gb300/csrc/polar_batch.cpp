@@ -110,7 +110,7 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
         b->alpha_elems = std::max(b->alpha_elems, 2 * s);
         b->beta_words = std::max(b->beta_words, code->NW);
         const size_t g = (code->N / 2 > s) ? size_t(code->N) - 2 * size_t(s) : 0;
-        b->gstride = std::max(b->gstride, g ? ((g * es + 15) / 16 * 16) / es : size_t(0));
+        b->gstride = std::max(b->gstride, g ? ((g * es + 127) / 128 * 128) / es : size_t(0));
     }
     // device tables of every code
     for (uint32_t c = 0; c < n_codes; ++c) {

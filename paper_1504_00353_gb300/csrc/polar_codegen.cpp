@@ -184,13 +184,61 @@ size_t emit_reg_op(std::ostream &o, const std::vector<HostOp> &ops, size_t i, ui
     return 1;
 }
 
+// In the per-lane form (kLocalLeaves), a split node of 4 to 16 leaves inside a
+// register subtree is decoded by every lane on its own (RegSub::lenter, lfg,
+// lr1, lrep, lspc; Combine and Rate-0 are the same word operations). If
+// operation i starts such a node, emits the node's operations in that form and
+// returns how many list entries it covered; otherwise 0.
+size_t emit_local_node(std::ostream &o, const std::vector<HostOp> &ops, size_t i, uint32_t o0,
+                       const char *indent) {
+    const HostOp &a = ops[i];
+    const uint32_t n = 1u << a.log2n;
+    if ((a.kind != OP_F && a.kind != OP_G0R) || n > 16 || n < 4 || (a.flags & OPW_REG_ENTER))
+        return 0;
+    size_t j = i + 1;  // the node's operations: offsets inside [off, off + n), sizes <= n
+    while (j < ops.size() && (ops[j].flags & OPW_REG) && !(ops[j].flags & OPW_REG_ENTER) &&
+           ops[j].off >= a.off && ops[j].off < a.off + n && ops[j].log2n <= a.log2n)
+        ++j;
+    for (size_t k = i; k < j; ++k)
+        if (ops[k].flags & OPW_REG_EXIT) return 0;  // the node is the subtree itself
+    o << indent << "r.template lenter<" << n << "u>();\n";
+    for (size_t k = i; k < j; ++k) {
+        const HostOp &op = ops[k];
+        const uint32_t m = 1u << op.log2n, p = op.off - o0;
+        o << indent << "r.template ";
+        switch (op.kind) {
+        case OP_F:
+        case OP_G:
+        case OP_G0R: o << "lfg<" << kind_name(op.kind) << ", " << m << "u, " << p << "u>();\n"; break;
+        case OP_C: o << "combine<" << m << "u, " << p << "u, false>();\n"; break;
+        case OP_C0R: o << "combine<" << m << "u, " << p << "u, true>();\n"; break;
+        case OP_R0: o << "r0<" << m << "u, " << p << "u>();\n"; break;
+        case OP_R1: o << "lr1<" << m << "u, " << p << "u>();\n"; break;
+        case OP_REP: o << "lrep<" << m << "u, " << p << "u>();\n"; break;
+        default: o << "lspc<" << m << "u, " << p << "u>();\n"; break;
+        }
+    }
+    return j - i;
+}
+
+// One register-subtree operation (or a per-lane node, or a fused
+// Repetition-SPC node) at list index i; returns the entries covered.
+size_t emit_reg_ops(std::ostream &o, const std::vector<HostOp> &ops, size_t i, uint32_t o0,
+                    const char *indent, bool local) {
+    if (local) {
+        const size_t used = emit_local_node(o, ops, i, o0, indent);
+        if (used) return used;
+    }
+    return emit_reg_op(o, ops, i, o0, indent);
+}
+
 // Compact form: one out-of-line function per distinct register subtree (the
 // operations with offsets relative to the subtree, so equal frozen patterns
 // share code), emitted before the body; returns, per list index of a subtree's
 // first operation, the function's id.
 std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std::vector<HostOp> &ops,
                                                 const char *T, uint32_t R,
-                                                const std::string &prefix) {
+                                                const std::string &prefix, bool local) {
     std::map<std::string, size_t> ids;
     std::map<size_t, size_t> at;
     for (size_t i = 0; i < ops.size(); ++i) {
@@ -198,7 +246,7 @@ std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std
         const uint32_t o0 = ops[i].off, n0 = 1u << ops[i].log2n;
         std::ostringstream b;
         for (size_t j = i;;) {
-            const size_t used = emit_reg_op(b, ops, j, o0, "  ");
+            const size_t used = emit_reg_ops(b, ops, j, o0, "  ", local);
             j += used;
             if (ops[j - 1].flags & OPW_REG_EXIT) break;
         }
@@ -269,13 +317,47 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
                uint32_t R, const std::string &name, uint32_t outline = 0,
                bool warp_frames = false, bool chan_global = true) {
     const bool outline_sub = outline & kOutlineSubtrees, outline_mem = outline & kOutlineMemory;
+    const bool local = outline & kLocalLeaves;
     const uint32_t N = code.N;
     const std::vector<HostOp> ops = code.build_ops(R);
     const std::vector<std::vector<uint32_t>> prefetch = plan_prefetch(ops, N, S, chan_global);
     const uint32_t es = is_i8 ? 1u : 4u;
+    // last[i]: operation i is the last to read its input stage before an
+    // operation rewrites it (a register subtree's entry reads its root stage)
+    auto reads = [&](size_t j) -> uint32_t {
+        return (ops[j].flags & OPW_REG_ENTER) ? (1u << ops[j].log2n) : mem_input_stage(ops[j]);
+    };
+    std::vector<bool> last(ops.size(), false);
+    for (size_t i = 0; i < ops.size(); ++i) {
+        const uint32_t n = reads(i);
+        if (!n || n == N) continue;  // the channel is never rewritten
+        bool more = false;
+        for (size_t j = i + 1; j < ops.size(); ++j) {
+            if (reads(j) == n) { more = true; break; }
+            if (mem_output_stage(ops[j]) == n) break;
+        }
+        last[i] = !more;
+    }
+    auto scratch = [&](uint32_t n) { return n < N && n > S; };
+    // how operation i reads its input (RD_*), and whether its input stage is
+    // discarded from L2 after it
+    auto rd_of = [&](size_t i) -> uint32_t {
+        const uint32_t n = reads(i);
+        if (n == N && chan_global) return RD_STREAM;
+        return (scratch(n) && last[i]) ? RD_LAST : RD_NORMAL;
+    };
+    auto discard = [&](size_t i, const char *grp, const char *indent) {
+        if (rd_of(i) != RD_LAST) return;
+        const uint32_t n = reads(i);
+        o << indent << "discard_l2<" << grp << ">(gen_in<T, N, S, " << n << "u>(fr), " << n * es
+          << "u);\n";
+    };
+    auto rd_name = [](uint32_t rd) {
+        return rd == RD_LAST ? "polar::RD_LAST" : (rd == RD_STREAM ? "polar::RD_STREAM" : "polar::RD_NORMAL");
+    };
     const char *T = is_i8 ? "int8_t" : "float";
     std::map<size_t, size_t> sub_at;
-    if (outline_sub) sub_at = emit_subtree_functions(o, ops, T, R, name + "_");
+    if (outline_sub) sub_at = emit_subtree_functions(o, ops, T, R, name + "_", local);
     o << "struct " << name << " {\n"
       << "  __device__ __forceinline__ void operator()(const Frame<" << T << "> &fr, float *) const {\n"
       << "    using T = " << T << ";\n"
@@ -295,15 +377,17 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     };
     // Memory-resident operation on the whole CTA or on warp 0 (inlined with
     // constant arguments: out-of-line copies measured slower).
-    auto mem_op = [&](const HostOp &op, const char *grp) {
+    auto mem_op = [&](size_t idx, const char *grp) {
+        const HostOp &op = ops[idx];
         const uint32_t n = 1u << op.log2n, off = op.off;
+        const char *rd = rd_name(rd_of(idx));
         if (outline_mem) {  // out-of-line calls with run-time sizes
             switch (op.kind) {
             case OP_F:
             case OP_G:
             case OP_G0R:
-                o << "      mem_fg<T, " << grp << ", " << kind_name(op.kind) << ">(" << in(n) << ", "
-                  << out(n / 2) << ", " << n / 2 << "u, fr.beta, " << off << "u);\n";
+                o << "      mem_fg<T, " << grp << ", " << kind_name(op.kind) << ", " << rd << ">("
+                  << in(n) << ", " << out(n / 2) << ", " << n / 2 << "u, fr.beta, " << off << "u);\n";
                 break;
             case OP_C:
             case OP_C0R:
@@ -330,8 +414,8 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
         case OP_F:
         case OP_G:
         case OP_G0R:
-            o << "      op_fg<T, " << grp << ", " << kind_name(op.kind) << ">(" << in(n) << ", "
-              << out(n / 2) << ", " << n / 2 << "u, fr.beta, " << off << "u);\n";
+            o << "      op_fg<T, " << grp << ", " << kind_name(op.kind) << ", " << rd << ">("
+              << in(n) << ", " << out(n / 2) << ", " << n / 2 << "u, fr.beta, " << off << "u);\n";
             break;
         case OP_C:
         case OP_C0R:
@@ -380,11 +464,14 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     auto chain_op = [&](size_t i, uint32_t len, const char *grp) {
         const HostOp &a = ops[i];
         const uint32_t n = 1u << a.log2n;
+        // an intermediate stage whose only reader is the next operation of the
+        // chain is not stored
+        const uint32_t store = (last[i + 1] ? 0u : 1u) | (len == 3 && last[i + 2] ? 0u : 2u);
         o << "      " << (outline_mem ? "mem_chain" : "op_chain") << "<T, " << grp << ", " << len
           << "u, " << kind_name(a.kind) << ", " << kind_name(ops[i + 1].kind) << ", "
-          << (len == 3 ? kind_name(ops[i + 2].kind) : "polar::OP_F") << ">(" << in(n) << ", "
-          << out(n / 2) << ", " << out(n / 4) << ", " << (len == 3 ? out(n / 8) : "nullptr")
-          << ", " << n << "u, fr.beta, " << a.off << "u);\n";
+          << (len == 3 ? kind_name(ops[i + 2].kind) : "polar::OP_F") << ", " << store << "u, "
+          << rd_name(rd_of(i)) << ">(" << in(n) << ", " << out(n / 2) << ", " << out(n / 4) << ", "
+          << (len == 3 ? out(n / 8) : "nullptr") << ", " << n << "u, fr.beta, " << a.off << "u);\n";
     };
 
     bool in_run = false;
@@ -401,8 +488,9 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             }
             o << "    {\n";
             if (clen > 1) chain_op(i, clen, "CtaGrp");
-            else mem_op(op, "CtaGrp");
+            else mem_op(i, "CtaGrp");
             o << "    }\n    __syncthreads();\n";
+            discard(i, "CtaGrp", "    ");
             i += clen - 1;
             continue;
         }
@@ -413,12 +501,14 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
         if (!(op.flags & OPW_REG) && clen > 1) {
             chain_op(i, clen, "WarpGrp");
             o << "      __syncwarp();\n";
+            discard(i, "WarpGrp", "      ");
             i += clen - 1;
             continue;
         }
         if (!(op.flags & OPW_REG)) {
-            mem_op(op, "WarpGrp");
+            mem_op(i, "WarpGrp");
             o << "      __syncwarp();\n";
+            discard(i, "WarpGrp", "      ");
             continue;
         }
         const char *align = warp_frames ? "      __syncthreads();\n" : "";
@@ -436,7 +526,7 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
             o << "      {\n        RegSub<T, " << R << "u> r;\n        r.lane = lane;\n"
               << "        r.template enter<" << n0 << "u>(" << in(n0) << ");\n";
         }
-        i += emit_reg_op(o, ops, i, o0, "        ") - 1;
+        i += emit_reg_ops(o, ops, i, o0, "        ", local) - 1;
         if (ops[i].flags & OPW_REG_EXIT) {
             o << "        r.template exit<" << n0 << "u>(fr.beta, " << o0 << "u);\n      }\n"
               << "      __syncwarp();\n" << align;

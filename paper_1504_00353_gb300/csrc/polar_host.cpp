@@ -165,7 +165,7 @@ polar_status choose_shape(const polar_code *c, bool is_i8, size_t n_frames, int 
     sh->stage_channel = stage;
     sh->smem_bytes = smem;
     const size_t g = (N / 2 > S) ? size_t(N) - 2 * size_t(S) : 0;
-    sh->scratch_elems_per_cta = g ? ((g * es + 15) / 16 * 16) / es : 0;
+    sh->scratch_elems_per_cta = g ? ((g * es + 127) / 128 * 128) / es : 0;
     sh->ctas_per_sm = 0;
     sh->grid = 0;
     return POLAR_OK;
@@ -683,11 +683,13 @@ polar_status polar_code_compile(polar_code_t *code, int is_i8, size_t n_frames,
 polar_status polar_code_compile_ex(polar_code_t *code, int is_i8, size_t n_frames,
                                    uint32_t reg_subtree, uint32_t flags) {
     if (!code) return POLAR_EINVAL;
-    if (flags & ~(POLAR_COMPILE_COMPACT | POLAR_COMPILE_FULL) ||
+    if (flags & ~(POLAR_COMPILE_COMPACT | POLAR_COMPILE_FULL | POLAR_COMPILE_LOCAL_LEAVES) ||
         (flags & POLAR_COMPILE_COMPACT && flags & POLAR_COMPILE_FULL))
         return POLAR_EINVAL;
+    const uint32_t form = flags & (POLAR_COMPILE_COMPACT | POLAR_COMPILE_FULL);
     uint32_t outline = flags & POLAR_COMPILE_COMPACT;  // subtrees (1) and/or memory ops (2)
-    if (!flags && code->ops.size() > kCompactOps) outline = kOutlineSubtrees | kOutlineMemory;
+    if (!form && code->ops.size() > kCompactOps) outline = kOutlineSubtrees | kOutlineMemory;
+    if (flags & POLAR_COMPILE_LOCAL_LEAVES) outline |= kLocalLeaves;
     if (reg_subtree == 0) reg_subtree = 256;
     if (!is_pow2(reg_subtree) || reg_subtree < 32 || reg_subtree > 1024) return POLAR_EINVAL;
     int device = -1;

@@ -275,6 +275,10 @@ namespace polar {
 // memory-resident operations out-of-line calls with run-time sizes. Both keep
 // very long operation lists (N = 2^20) compilable.
 constexpr uint32_t kOutlineSubtrees = 1u, kOutlineMemory = 2u;
+// Split nodes of 4 to 16 leaves inside register subtrees in the per-lane form
+// (every lane decodes the node alone; see RegSub::lenter): shorter dependent
+// chains for one frame in flight.
+constexpr uint32_t kLocalLeaves = 4u;
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
                             uint32_t reg_subtree, uint32_t outline = 0);
 // Source of the mixed-batch decoder: one specialised body per code (per-code

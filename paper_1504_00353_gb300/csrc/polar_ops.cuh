@@ -46,6 +46,13 @@ enum OpKind : uint32_t {
     OP_SPC = 8,   // SPC: hard decisions, flip least-|alpha| bit on odd parity
 };
 
+// How an operation reads its input stage: RD_NORMAL; RD_STREAM, an L2
+// evict-first policy (the channel LLRs, read far apart in time); RD_LAST, the
+// last read of a scratch stage before it is rewritten: evict-first, and the
+// generated code then discards the lines (discard_l2) so that the dead data is
+// never written back to DRAM. Hints only: the values read are the same.
+enum : uint32_t { RD_NORMAL = 0, RD_STREAM = 1, RD_LAST = 2 };
+
 // One operation as the interpreter reads it: a 32-bit word
 //   bits 0-3   kind (OpKind)
 //   bits 4-8   log2(N_v)
@@ -242,6 +249,39 @@ template <> struct Llr<int8_t> {
     using Vec = uint4;
 };
 
+// ---------------------------------------------------------------- hinted device-memory reads
+
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+template <uint32_t RD>
+__device__ __forceinline__ uint4 ldv(const uint4 *p, unsigned long long pol) {
+    if constexpr (RD == RD_NORMAL) {
+        return *p;
+    } else {
+        uint4 r;
+        asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p), "l"(pol) : "memory");
+        return r;
+    }
+}
+template <uint32_t RD>
+__device__ __forceinline__ float4 ldv(const float4 *p, unsigned long long pol) {
+    if constexpr (RD == RD_NORMAL) {
+        return *p;
+    } else {
+        float4 r;
+        asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p), "l"(pol) : "memory");
+        return r;
+    }
+}
+__device__ __forceinline__ unsigned long long policy_for(uint32_t rd) {
+    return rd == RD_NORMAL ? 0ull : evict_first_policy();
+}
+
 // ---------------------------------------------------------------- groups
 
 struct WarpGrp {
@@ -256,6 +296,17 @@ struct CtaGrp {
     __device__ static uint32_t size() { return blockDim.x; }
     __device__ static void sync() { __syncthreads(); }
 };
+
+// Drop [p, p + bytes) of a scratch stage from L2 without writing it back
+// (discard.global.L2: afterwards the bytes are undefined until written again).
+// Call after a group barrier that follows the stage's last read; p 128-byte
+// aligned, bytes a multiple of 128.
+template <class Grp>
+__device__ __forceinline__ void discard_l2(const void *p, uint32_t bytes) {
+    for (uint32_t off = Grp::rank() * 128u; off < bytes; off += Grp::size() * 128u)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(static_cast<const char *>(p) + off)
+                     : "memory");
+}
 
 // ---------------------------------------------------------------- beta helpers
 
@@ -322,7 +373,7 @@ __device__ __forceinline__ T fg_scalar(T a, T b, uint32_t bit) {
 // out[i] = op(in[i], in[i + h]) for i < h; in and out never overlap. Four vectors
 // per thread are loaded before any is used, so device-memory operands (the
 // channel at the root, scratch stages) overlap their latency.
-template <typename T, class Grp, uint32_t KIND>
+template <typename T, class Grp, uint32_t KIND, uint32_t RD = RD_NORMAL>
 __device__ __forceinline__ void op_fg(const T *__restrict__ in, T *__restrict__ out, uint32_t h,
                                       const uint32_t *beta, uint32_t o) {
     using Vec = typename Llr<T>::Vec;
@@ -332,13 +383,14 @@ __device__ __forceinline__ void op_fg(const T *__restrict__ in, T *__restrict__ 
         const Vec *va = reinterpret_cast<const Vec *>(in);
         const Vec *vb = reinterpret_cast<const Vec *>(in + h);
         Vec *vo = reinterpret_cast<Vec *>(out);
+        const unsigned long long pol = policy_for(RD);
         uint32_t v = Grp::rank();
         for (; v + 3 * G < nv; v += 4 * G) {
             Vec a[4], b[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                a[k] = va[v + k * G];
-                b[k] = vb[v + k * G];
+                a[k] = ldv<RD>(va + v + k * G, pol);
+                b[k] = ldv<RD>(vb + v + k * G, pol);
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -348,7 +400,7 @@ __device__ __forceinline__ void op_fg(const T *__restrict__ in, T *__restrict__ 
         }
         for (; v < nv; v += G) {
             const uint32_t bits = KIND == OP_G ? bits_at(beta, o + v * V, V) : 0u;
-            vo[v] = fg4<KIND>(va[v], vb[v], bits);
+            vo[v] = fg4<KIND>(ldv<RD>(va + v, pol), ldv<RD>(vb + v, pol), bits);
         }
     } else {
         for (uint32_t i = Grp::rank(); i < h; i += Grp::size()) {
@@ -368,7 +420,11 @@ __device__ __forceinline__ void op_fg(const T *__restrict__ in, T *__restrict__ 
 // reads it again) and the last one. Element by element this is the same
 // arithmetic as the L operations one after another. stage1/2/3 = stages n/2,
 // n/4, n/8; (n >> L) must be a multiple of the vector width.
-template <typename T, class Grp, uint32_t L, uint32_t K0, uint32_t K1, uint32_t K2>
+// STORE: bit 0 stores stage n/2, bit 1 stage n/4 (for L = 3; the last stage
+// is always stored): an intermediate stage that no later operation reads is
+// not written at all. RD: how the input stage is read (see RD_LAST).
+template <typename T, class Grp, uint32_t L, uint32_t K0, uint32_t K1, uint32_t K2,
+          uint32_t STORE = 3u, uint32_t RD = RD_NORMAL>
 __device__ __forceinline__ void op_chain(const T *__restrict__ in, T *__restrict__ stage1,
                                          T *__restrict__ stage2, T *__restrict__ stage3,
                                          uint32_t n, const uint32_t *beta, uint32_t o) {
@@ -379,22 +435,23 @@ __device__ __forceinline__ void op_chain(const T *__restrict__ in, T *__restrict
     Vec *v1 = reinterpret_cast<Vec *>(stage1);
     Vec *v2 = reinterpret_cast<Vec *>(stage2);
     Vec *v3 = reinterpret_cast<Vec *>(stage3);
+    const unsigned long long pol = policy_for(RD);
     for (uint32_t c = Grp::rank(); c < nvc; c += Grp::size()) {
         Vec x[M];
 #pragma unroll
-        for (uint32_t m = 0; m < M; ++m) x[m] = vi[c + m * nvc];
+        for (uint32_t m = 0; m < M; ++m) x[m] = ldv<RD>(vi + c + m * nvc, pol);
         Vec y[M / 2];
 #pragma unroll
         for (uint32_t m = 0; m < M / 2; ++m) {
             const uint32_t bits = K0 == OP_G ? bits_at(beta, o + (c + m * nvc) * V, V) : 0u;
             y[m] = fg4<K0>(x[m], x[m + M / 2], bits);
-            v1[c + m * nvc] = y[m];
+            if (STORE & 1u) v1[c + m * nvc] = y[m];
         }
         Vec z[M / 4];
 #pragma unroll
         for (uint32_t m = 0; m < M / 4; ++m) {
             z[m] = fg4<K1>(y[m], y[m + M / 4], 0u);
-            v2[c + m * nvc] = z[m];
+            if (L == 2 || (STORE & 2u)) v2[c + m * nvc] = z[m];
         }
         if constexpr (L == 3) v3[c] = fg4<K2>(z[0], z[1], 0u);
     }
@@ -877,15 +934,16 @@ __device__ __forceinline__ void run_warp_frames(const KernelArgs &a, const Body 
 // The memory-resident operations as real calls with run-time sizes: the compact
 // form of a generated decoder uses them so that code size grows with the number
 // of distinct subtrees, not with the length of the operation list.
-template <typename T, class Grp, uint32_t KIND>
+template <typename T, class Grp, uint32_t KIND, uint32_t RD = RD_NORMAL>
 __device__ __noinline__ void mem_fg(const T *in, T *out, uint32_t h, const uint32_t *beta,
                                     uint32_t o) {
-    op_fg<T, Grp, KIND>(in, out, h, beta, o);
+    op_fg<T, Grp, KIND, RD>(in, out, h, beta, o);
 }
-template <typename T, class Grp, uint32_t L, uint32_t K0, uint32_t K1, uint32_t K2>
+template <typename T, class Grp, uint32_t L, uint32_t K0, uint32_t K1, uint32_t K2,
+          uint32_t STORE = 3u, uint32_t RD = RD_NORMAL>
 __device__ __noinline__ void mem_chain(const T *in, T *stage1, T *stage2, T *stage3, uint32_t n,
                                        const uint32_t *beta, uint32_t o) {
-    op_chain<T, Grp, L, K0, K1, K2>(in, stage1, stage2, stage3, n, beta, o);
+    op_chain<T, Grp, L, K0, K1, K2, STORE, RD>(in, stage1, stage2, stage3, n, beta, o);
 }
 template <class Grp>
 __device__ __noinline__ void mem_combine(uint32_t *beta, uint32_t n, uint32_t o, bool copy) {
@@ -988,6 +1046,7 @@ struct RegSub {
     using Acc = typename Llr<T>::Acc;
     static constexpr uint32_t NWORD = R >= 32 ? R / 32 : 1;
     Acc s1024[32], s512[16], s256[8], s128[4], s64[2], s32, A;
+    Acc l16[16], l8[8], l4[4], l2[2], l1;  // the per-lane form of nodes of <= 16 leaves
     uint32_t bw[NWORD];
     uint32_t lane;
 
@@ -1171,6 +1230,79 @@ struct RegSub {
             x = __shfl_sync(kFull, x, n);
             set_field<p / 32, p % 32, n>(x < Acc(0) ? kFull : 0u);
         }
+    }
+
+    // ---- Per-lane form of a node of at most 16 leaves: every lane copies the
+    // node's LLRs and decodes the whole node on its own, with no shuffles. Each
+    // operation is the same arithmetic in the same order as its shuffle form
+    // (F, G, the Repetition fold t[i] + t[i + m], the lowest-index SPC flip),
+    // and the bits land in the same warp-uniform words. Fewer dependent steps
+    // per operation than the shuffle form, more instructions: for one frame
+    // in flight (latency), not for many.
+    template <uint32_t m, uint32_t k>
+    __device__ __forceinline__ Acc &loc() {
+        if constexpr (m == 16) return l16[k];
+        else if constexpr (m == 8) return l8[k];
+        else if constexpr (m == 4) return l4[k];
+        else if constexpr (m == 2) return l2[k];
+        else return l1;
+    }
+
+    // Stage n0 (register A, lanes [n0, 2 n0)) to every lane.
+    template <uint32_t n0>
+    __device__ __forceinline__ void lenter() {
+        static_for<0, n0>([&](auto kc) {
+            constexpr uint32_t k = decltype(kc)::value;
+            loc<n0, k>() = __shfl_sync(kFull, A, n0 + k);
+        });
+    }
+
+    template <uint32_t KIND, uint32_t n, uint32_t p>
+    __device__ __forceinline__ void lfg() {
+        constexpr uint32_t h = n / 2;
+        static_for<0, h>([&](auto kc) {
+            constexpr uint32_t k = decltype(kc)::value;
+            const Acc x = loc<n, k>(), y = loc<n, k + h>();
+            Acc r;
+            if constexpr (KIND == OP_F) r = op_f(x, y);
+            else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32] >> ((p % 32) + k)) & 1u);
+            else r = op_add(x, y);
+            loc<h, k>() = r;
+        });
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ uint32_t lhard() {
+        uint32_t b = 0;
+        static_for<0, n>([&](auto kc) {
+            constexpr uint32_t k = decltype(kc)::value;
+            b |= (loc<n, k>() < Acc(0) ? 1u : 0u) << k;
+        });
+        return b;
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void lr1() { set_field<p / 32, p % 32, n>(lhard<n, p>()); }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void lrep() {
+        Acc t[n];
+        static_for<0, n>([&](auto kc) { t[decltype(kc)::value] = loc<n, decltype(kc)::value>(); });
+        fold_local<n>(t);
+        set_field<p / 32, p % 32, n>(t[0] < Acc(0) ? kFull : 0u);
+    }
+
+    template <uint32_t n, uint32_t p>
+    __device__ __forceinline__ void lspc() {
+        const uint32_t hd = lhard<n, p>();
+        uint32_t best = mag_bits(loc<n, 0>()), at = 0;
+        static_for<1, n>([&](auto kc) {
+            constexpr uint32_t k = decltype(kc)::value;
+            const uint32_t mg = mag_bits(loc<n, k>());
+            at = mg < best ? k : at;  // strictly smaller: the lowest index keeps a tie
+            best = mg < best ? mg : best;
+        });
+        set_field<p / 32, p % 32, n>(hd ^ ((__popc(hd) & 1u) << at));
     }
 
     // Repetition-SPC node of n leaves (8 or 16) at subtree offset p, decoded

@@ -322,13 +322,15 @@ def polar_code_set_frames_per_cta(code: PolarCode, is_i8: bool, frames: int):
 
 
 COMPILE_OUTLINE_SUBTREES, COMPILE_OUTLINE_MEMORY, COMPILE_COMPACT, COMPILE_FULL = 1, 2, 3, 4
+COMPILE_LOCAL_LEAVES = 8
 
 
 def polar_code_compile(code: PolarCode, is_i8: bool, n_frames: int, reg_subtree: int = 0,
                        flags: int = 0):
     """Compile the decoder specialised to this code for the shape of an n_frames
     decode (flags: COMPILE_OUTLINE_SUBTREES, COMPILE_OUTLINE_MEMORY, COMPILE_COMPACT,
-    COMPILE_FULL to force a form)."""
+    COMPILE_FULL to force a form; COMPILE_LOCAL_LEAVES for the per-lane form of small
+    nodes)."""
     st = _lib.polar_code_compile_ex(code.handle, int(bool(is_i8)), n_frames, reg_subtree, flags)
     if st != 0:
         raise PolarError(st, "polar_code_compile: " + polar_code_compile_log(code)[-2000:])

@@ -108,9 +108,9 @@ def test_repspc_heavy_masks(seed):
     yi = rng.integers(-127, 128, (300, N)).astype(np.int8)
     yi[:, ::7] = 127
     for y, i8 in ((y32, False), (yi, True)):
-        for reg in (32, 256):
+        for reg, flags in ((32, 0), (256, 0), (256, polar.COMPILE_LOCAL_LEAVES)):
             c = polar.polar_code_create(N, K, mask)
-            polar.polar_code_compile(c, i8, 300, reg)
+            polar.polar_code_compile(c, i8, 300, reg, flags)
             assert polar.polar_code_get_launch(c, i8, 300)["unrolled"] == reg
             assert np.array_equal(decode(c, y, i8), oracle.decode_batch(mask, y))
 
@@ -226,3 +226,35 @@ def test_frames_per_cta_memory_level_nodes(F):
         polar.polar_code_compile(code, i8, 257, 256)
         assert polar.polar_code_get_launch(code, i8, 257)["frames_per_cta"] == F
         assert np.array_equal(decode(code, y, i8), oracle.decode_batch(mask, y))
+
+
+@pytest.mark.parametrize("i8", [False, True])
+@pytest.mark.parametrize("N,reg", [(64, 64), (1024, 256), (4096, 1024)])
+def test_local_leaves_random_masks(i8, N, reg):
+    """The per-lane form of split nodes of 4 to 16 leaves (every lane decodes
+    the node on its own) gives the oracle's bits on random masks, including
+    ties in int8 (small integer LLRs), at batch and batch-1 shapes."""
+    rng = np.random.default_rng(N + reg + i8)
+    for trial in range(3):
+        K = int(rng.integers(1, N))
+        mask = _cases.random_mask(rng, N, K)
+        y = rng.integers(-6, 7, (150, N)).astype(np.int8) if i8 else \
+            (rng.standard_normal((150, N)) * 3).astype(np.float32)
+        for n in (150, 1):
+            code = polar.polar_code_create(N, K, mask)
+            polar.polar_code_compile(code, i8, n, reg, polar.COMPILE_LOCAL_LEAVES)
+            assert polar.polar_code_get_launch(code, i8, n)["unrolled"] == reg
+            assert np.array_equal(decode(code, y[:n], i8), oracle.decode_batch(mask, y[:n]))
+
+
+@pytest.mark.parametrize("i8", [False, True])
+def test_local_leaves_n32768_batch1(i8):
+    """(32768, 29492) batch-1 shape with the per-lane small-node form and
+    Repetition-SPC-heavy masks."""
+    mask, d, llr = _cases.frames(32768, 29492, 4.0, 3, seed=43)
+    y = synth.quantize_i8(llr) if i8 else llr
+    code = polar.polar_code_create(32768, 29492, mask)
+    polar.polar_code_set_launch(code, i8, threads=256, warp_stage_max=1024)
+    polar.polar_code_compile(code, i8, 1, 1024, polar.COMPILE_LOCAL_LEAVES)
+    for f in range(3):
+        assert np.array_equal(decode(code, y[f:f + 1], i8), oracle.decode_batch(mask, y[f:f + 1]))
