@@ -263,6 +263,10 @@ class CodeTuner:
                         ctas_per_sm=0)
         if fixed_threads is None:
             self.measure([default(t) for t in threads_options])
+            # one warp per frame, several frames per CTA, at two stage caps
+            if tune_ctas:
+                self.measure([dict(default(32), frames_per_cta=f, smem_stage_max=s)
+                              for f in (2, 4) for s in (512, 1024)])
             cur, _ = self.best()
         else:
             self.measure([default(fixed_threads)])

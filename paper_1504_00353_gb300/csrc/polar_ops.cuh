@@ -525,6 +525,42 @@ __device__ __forceinline__ void op_r1_i8v(const int8_t *__restrict__ in, uint32_
     }
 }
 
+// Rate-1 (Eq. 4) on float32 LLRs, n >= 128: four values per lane per 16-byte
+// load; the eight lanes 8w..8w+7 of a warp hold the 32 values of one beta word
+// and OR their 4-bit pieces together with three shuffles. Four loads per lane
+// are in flight before the first is used.
+template <class Grp>
+__device__ __forceinline__ void op_r1_f32v(const float *__restrict__ in, uint32_t *beta,
+                                           uint32_t n, uint32_t o) {
+    const float4 *v = reinterpret_cast<const float4 *>(in);
+    const uint32_t nv = n >> 2, lane = threadIdx.x & 31u;
+    const uint32_t w0 = Grp::kCta ? (threadIdx.x & ~31u) : 0u;
+    const uint32_t step = Grp::kCta ? blockDim.x : 32u;
+    for (uint32_t base = w0; base < nv; base += 4 * step) {
+        uint32_t m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t i = base + k * step + lane;
+            uint32_t b = 0;
+            if (i < nv) {
+                const float4 x = v[i];
+                b = (__float_as_uint(x.x) >> 31) | ((__float_as_uint(x.y) >> 30) & 2u) |
+                    ((__float_as_uint(x.z) >> 29) & 4u) | ((__float_as_uint(x.w) >> 28) & 8u);
+            }
+            m[k] = b << (4u * (lane & 7u));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t i = base + k * step + lane;
+            uint32_t w = m[k];
+            w |= __shfl_xor_sync(kFull, w, 1);
+            w |= __shfl_xor_sync(kFull, w, 2);
+            w |= __shfl_xor_sync(kFull, w, 4);
+            if (i < nv && !(lane & 7u)) beta[(o >> 5) + (i >> 3)] = w;
+        }
+    }
+}
+
 // Rate-1 (Eq. 4): one ballot per 32 consecutive elements; four chunks loaded ahead.
 template <typename T, class Grp>
 __device__ __forceinline__ void op_r1(const T *__restrict__ in, uint32_t *beta, uint32_t n,
@@ -532,6 +568,11 @@ __device__ __forceinline__ void op_r1(const T *__restrict__ in, uint32_t *beta, 
     if constexpr (sizeof(T) == 1) {
         if (n >= 32) {
             op_r1_i8v<Grp>(reinterpret_cast<const int8_t *>(in), beta, n, o);
+            return;
+        }
+    } else {
+        if (n >= 128) {
+            op_r1_f32v<Grp>(reinterpret_cast<const float *>(in), beta, n, o);
             return;
         }
     }
