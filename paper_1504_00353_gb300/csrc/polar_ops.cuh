@@ -1076,6 +1076,23 @@ __device__ __forceinline__ void static_for(F &&f) {
     }
 }
 
+// Register-subtree arithmetic. Both LLR types are held in float registers:
+// int8 LLRs are integers in [-127, 127], exact in float, and every sum of two
+// of them is exact too. int8 keeps its saturation: each G and each Repetition
+// fold is clamped to [-127, 127], which is what the saturating byte add
+// followed by max(-127) gives. F is one min.xorsign.abs for both types.
+template <typename T>
+__device__ __forceinline__ float sat_reg(float v) {
+    if constexpr (sizeof(T) == 1) return fminf(fmaxf(v, -127.0f), 127.0f);
+    else return v;
+}
+template <typename T>
+__device__ __forceinline__ float rop_f(float a, float b) { return f_f32(a, b); }
+template <typename T>
+__device__ __forceinline__ float rop_g(float a, float b, uint32_t bit) { return sat_reg<T>(g_f32(a, b, bit)); }
+template <typename T>
+__device__ __forceinline__ float rop_add(float a, float b) { return sat_reg<T>(a + b); }
+
 // Subtree of at most R leaves decoded by warp 0 with compile-time node sizes and
 // offsets (the generated decoders): stage m >= 32 is m/32 registers per lane
 // (element j + 32k in register k of lane j), stages 1..16 share register A
@@ -1084,7 +1101,7 @@ __device__ __forceinline__ void static_for(F &&f) {
 // F and G above 32 leaves are lane-local; at 32 and below they are shuffles.
 template <typename T, uint32_t R>
 struct RegSub {
-    using Acc = typename Llr<T>::Acc;
+    using Acc = float;  // both LLR types (see rop_f)
     static constexpr uint32_t NWORD = R >= 32 ? R / 32 : 1;
     Acc s1024[32], s512[16], s256[8], s128[4], s64[2], s32, A;
     Acc l16[16], l8[8], l4[4], l2[2], l1;  // the per-lane form of nodes of <= 16 leaves
@@ -1162,9 +1179,9 @@ struct RegSub {
                 constexpr uint32_t k = decltype(kc)::value;
                 const Acc x = reg<n, k>(), y = reg<n, k + K>();
                 Acc r;
-                if constexpr (KIND == OP_F) r = op_f(x, y);
-                else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32 + k] >> lane) & 1u);
-                else r = op_add(x, y);
+                if constexpr (KIND == OP_F) r = rop_f<T>(x, y);
+                else if constexpr (KIND == OP_G) r = rop_g<T>(x, y, (bw[p / 32 + k] >> lane) & 1u);
+                else r = rop_add<T>(x, y);
                 reg<n / 2, k>() = r;
             });
         } else if constexpr (n == 32) {
@@ -1172,9 +1189,9 @@ struct RegSub {
             const Acc x = __shfl_up_sync(kFull, s32, 16);
             const Acc y = s32;
             Acc r;
-            if constexpr (KIND == OP_F) r = op_f(x, y);
-            else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32] >> ((lane - 16) & 31u)) & 1u);
-            else r = op_add(x, y);
+            if constexpr (KIND == OP_F) r = rop_f<T>(x, y);
+            else if constexpr (KIND == OP_G) r = rop_g<T>(x, y, (bw[p / 32] >> ((lane - 16) & 31u)) & 1u);
+            else r = rop_add<T>(x, y);
             if (lane >= 16) A = r;
         } else {
             constexpr uint32_t h = n / 2, q = p % 32;
@@ -1182,9 +1199,9 @@ struct RegSub {
             const Acc x = __shfl_down_sync(kFull, A, h);
             const Acc y = __shfl_down_sync(kFull, A, n);
             Acc r;
-            if constexpr (KIND == OP_F) r = op_f(x, y);
-            else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32] >> ((q + lane - h) & 31u)) & 1u);
-            else r = op_add(x, y);
+            if constexpr (KIND == OP_F) r = rop_f<T>(x, y);
+            else if constexpr (KIND == OP_G) r = rop_g<T>(x, y, (bw[p / 32] >> ((q + lane - h) & 31u)) & 1u);
+            else r = rop_add<T>(x, y);
             if (lane >= h && lane < 2 * h) A = r;
         }
     }
@@ -1234,7 +1251,7 @@ struct RegSub {
         if constexpr (K > 1) {
             static_for<0, K / 2>([&](auto kc) {
                 constexpr uint32_t k = decltype(kc)::value;
-                t[k] = op_add(t[k], t[k + K / 2]);
+                t[k] = rop_add<T>(t[k], t[k + K / 2]);
             });
             fold_local<K / 2>(reinterpret_cast<Acc(&)[K / 2]>(t));
         }
@@ -1256,7 +1273,7 @@ struct RegSub {
 #pragma unroll
             for (uint32_t m = 16; m >= 1; m /= 2) {
                 const Acc y = __shfl_down_sync(kFull, x, m);
-                if (lane < m) x = op_add(x, y);
+                if (lane < m) x = rop_add<T>(x, y);
             }
             x = __shfl_sync(kFull, x, 0);
             const uint32_t word = x < Acc(0) ? kFull : 0u;
@@ -1266,7 +1283,7 @@ struct RegSub {
 #pragma unroll
             for (uint32_t m = n / 2; m >= 1; m /= 2) {
                 const Acc y = __shfl_down_sync(kFull, x, m);
-                if (lane >= n && lane < n + m) x = op_add(x, y);
+                if (lane >= n && lane < n + m) x = rop_add<T>(x, y);
             }
             x = __shfl_sync(kFull, x, n);
             set_field<p / 32, p % 32, n>(x < Acc(0) ? kFull : 0u);
@@ -1305,9 +1322,9 @@ struct RegSub {
             constexpr uint32_t k = decltype(kc)::value;
             const Acc x = loc<n, k>(), y = loc<n, k + h>();
             Acc r;
-            if constexpr (KIND == OP_F) r = op_f(x, y);
-            else if constexpr (KIND == OP_G) r = op_g(x, y, (bw[p / 32] >> ((p % 32) + k)) & 1u);
-            else r = op_add(x, y);
+            if constexpr (KIND == OP_F) r = rop_f<T>(x, y);
+            else if constexpr (KIND == OP_G) r = rop_g<T>(x, y, (bw[p / 32] >> ((p % 32) + k)) & 1u);
+            else r = rop_add<T>(x, y);
             loc<h, k>() = r;
         });
     }
@@ -1359,14 +1376,14 @@ struct RegSub {
         const bool act = lane < h;
         const Acc x = __shfl_sync(kFull, A, (n + lane) & 31u);      // alpha_v[i], i = lane
         const Acc y = __shfl_sync(kFull, A, (n + h + lane) & 31u);  // alpha_v[i + h]
-        Acc s = op_f(x, y);
+        Acc s = rop_f<T>(x, y);
 #pragma unroll
         for (uint32_t m = h / 2; m >= 1; m /= 2) {
             const Acc t = __shfl_down_sync(kFull, s, m);
-            if (lane < m) s = op_add(s, t);
+            if (lane < m) s = rop_add<T>(s, t);
         }
         const bool one = __shfl_sync(kFull, s, 0) < Acc(0);
-        const Acc g0 = op_g(x, y, 0u), g1 = op_g(x, y, 1u);
+        const Acc g0 = rop_g<T>(x, y, 0u), g1 = rop_g<T>(x, y, 1u);
         const uint32_t hd0 = __ballot_sync(kFull, act && g0 < Acc(0));
         const uint32_t hd1 = __ballot_sync(kFull, act && g1 < Acc(0));
         const uint32_t m0 = act ? mag_bits(g0) : kFull, m1 = act ? mag_bits(g1) : kFull;
