@@ -457,6 +457,8 @@ def run_native(args, world, rank, local):
     mask, code0, d, llr32 = make_inputs(wl, batch, wl["seed"] + 1000 * rank, "f32")
     llr_by_dtype = {"f32": llr32, "i8": synth.quantize_i8(llr32)}
 
+    forms = {}
+
     def setup(dtype):
         """Code handle with its specialised decoder compiled (untimed set-up)."""
         i8 = dtype == "i8"
@@ -464,6 +466,8 @@ def run_native(args, world, rank, local):
         shape, _ = tuned_or(N, K, mask, dtype)
         shape.setdefault("stage_channel", 2)
         compile_shape(code, dtype, shape, batch, args.interpreter, args.compile_form)
+        forms[dtype] = (args.compile_form if args.compile_form != "auto"
+                        else shape.get("compile_form", "auto"))
         return code
 
     def throughput(dtype, steps, warmup):
@@ -568,7 +572,7 @@ def run_native(args, world, rank, local):
                    "l2": (f"{r['n_buf']} distinct input buffer(s) of {r['in_bytes'] / 2**20:.0f} MiB "
                           "rotated; inputs larger than L2"),
                    "decoder": "interpreter" if args.interpreter else
-                   f"specialised (NVRTC, {args.compile_form} form)",
+                   f"specialised (NVRTC, {forms.get(main, 'auto')} form)",
                    "launch": r["launch"], "fer_check": r["fer"]},
         "latency_us": lat,
         "e2e": {"value": e2e_gbps, "unit": "Gbps",

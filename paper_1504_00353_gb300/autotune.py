@@ -103,9 +103,9 @@ def frames_for(N: int, sms: int) -> int:
 
 
 SHAPE_KEYS = ("threads", "smem_stage_max", "warp_stage_max", "ctas_per_sm", "stage_channel",
-              "reg_subtree", "frames_per_cta", "local_leaves")
+              "reg_subtree", "frames_per_cta", "local_leaves", "compile_form")
 SHAPE_DEFAULTS = dict(ctas_per_sm=0, stage_channel=2, reg_subtree=256, frames_per_cta=1,
-                      local_leaves=0)
+                      local_leaves=0, compile_form="auto")
 
 
 def _shape_key(s: dict) -> tuple:
@@ -125,7 +125,8 @@ def apply_shape(code, dtype: str, shape: dict, n_frames: int):
                                 ctas_per_sm=sh["ctas_per_sm"], stage_channel=sh["stage_channel"])
     polar.polar_code_set_frames_per_cta(code, dtype == "i8", sh["frames_per_cta"])
     polar.polar_code_compile(code, dtype == "i8", n_frames, sh["reg_subtree"],
-                             polar.COMPILE_LOCAL_LEAVES if sh["local_leaves"] else 0)
+                             COMPILE_FORM[sh["compile_form"]] |
+                             (polar.COMPILE_LOCAL_LEAVES if sh["local_leaves"] else 0))
 
 
 def _compile(N, K, mask, dtype, shape, n_frames):
@@ -285,6 +286,9 @@ class CodeTuner:
                 self.measure([dict(cur, frames_per_cta=f,
                                    ctas_per_sm=(cur["ctas_per_sm"] + f - 1) // f if cur["ctas_per_sm"] else 0)
                               for f in (2, 4)])
+            cur, _ = self.best(T)
+            # the inlined decoder against one with shared code for equal subtrees
+            self.measure([dict(cur, compile_form=f) for f in ("auto", "subtrees")])
         return self.best(T)
 
 
@@ -488,6 +492,9 @@ def configure(code, dtype: str, shape: dict, n_frames: int, interpreter: bool = 
     reg = sh.pop("reg_subtree", 0)
     fpc = sh.pop("frames_per_cta", 1)
     local = polar.COMPILE_LOCAL_LEAVES if sh.pop("local_leaves", 0) else 0
+    tuned_form = sh.pop("compile_form", "auto")
+    if form == "auto":  # an explicit form from the caller wins over the table's
+        form = tuned_form
     polar.polar_code_set_launch(code, dtype == "i8", **sh)
     polar.polar_code_set_frames_per_cta(code, dtype == "i8", fpc)
     if not interpreter:

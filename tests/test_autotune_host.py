@@ -26,7 +26,8 @@ def test_keys_and_lookup_fallback():
 
 def test_shape_tuple_roundtrip():
     s = dict(threads=128, smem_stage_max=2048, warp_stage_max=1024, ctas_per_sm=8,
-             stage_channel=1, reg_subtree=512, frames_per_cta=1, local_leaves=1)
+             stage_channel=1, reg_subtree=512, frames_per_cta=1, local_leaves=1,
+             compile_form="subtrees")
     assert autotune._shape(autotune._shape_key(s)) == s
     # defaults fill missing keys
     k = autotune._shape_key(dict(threads=32, smem_stage_max=256, warp_stage_max=2048))
