@@ -446,9 +446,6 @@ def main(argv=None):
         del tuners
 
 
-if __name__ == "__main__":
-    main()
-
 
 # ---------------------------------------------------------------- shapes in use
 
@@ -513,3 +510,7 @@ def batch_shape(dtype: str):
         return dict(threads=e["threads"], smem_stage_max=e["smem_stage_max"],
                     warp_stage_max=e["warp_stage_max"], ctas_per_sm=e.get("ctas_per_sm", 0)), "tuned"
     return dict(threads=32, smem_stage_max=None, warp_stage_max=None, ctas_per_sm=0), "default"
+
+
+if __name__ == "__main__":
+    main()

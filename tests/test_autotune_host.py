@@ -55,3 +55,20 @@ def test_committed_table_is_well_formed():
             assert parts[3] in ("f32", "i8") and int(parts[0]) >= int(parts[1])
             assert e["threads"] % 32 == 0 and e["threads"] <= 1024
             assert ("latency_us" in e) == key.endswith("_lat")
+
+
+def test_module_entry_point_defines_everything_it_uses():
+    """Run as a script (python -m ... --help), the module has every name its
+    tuning path uses defined before main() runs."""
+    import runpy
+    import sys
+
+    import pytest
+    argv = sys.argv
+    sys.argv = ["autotune", "--help"]
+    try:
+        with pytest.raises(SystemExit):
+            g = runpy.run_module("paper_1504_00353_gb300.autotune", run_name="__main__")
+    finally:
+        sys.argv = argv
+    assert autotune.SHAPE_DEFAULTS["compile_form"] in autotune.COMPILE_FORM
