@@ -55,17 +55,33 @@ def _embed_ops_header() -> None:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit in parallel (one nvcc per source, object
+    files in _build/), then link the shared library."""
     if not force and not _stale():
         return LIB
     _embed_ops_header()
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
-           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + GEN, "-o", tmp, *SOURCES,
-           "-ldl", "-lpthread"]
+    from concurrent.futures import ThreadPoolExecutor
+    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH, "-lineinfo",
+              "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + GEN]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+        common.insert(0, "-Xptxas=-v")
+    tag = f".{os.getpid()}.o"
+    objs = [os.path.join(GEN, os.path.basename(src) + tag) for src in SOURCES]
+
+    def compile_one(pair):
+        src, obj = pair
+        subprocess.run([nvcc(), *common, "-c", src, "-o", obj], check=True)
+
+    try:
+        with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+            list(ex.map(compile_one, zip(SOURCES, objs)))
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-ldl", "-lpthread"], check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 
