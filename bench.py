@@ -785,7 +785,8 @@ def run_serve(args):
     codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
     bshape, bsrc = batch_shape("f32")
     batch = polar.polar_batch_create(codes, False, bshape["threads"], bshape["smem_stage_max"],
-                                     bshape["warp_stage_max"], bshape["ctas_per_sm"])
+                                     bshape["warp_stage_max"], bshape["ctas_per_sm"],
+                                     bshape.get("flags", 0))
     budget = 4 << 30
     arms = {"served": dict(flags=0, slots=4, max_frames=4096),
             "plain": dict(flags=polar.SERVE_LAUNCH_PER_CODE, slots=1, max_frames=4096)}
@@ -938,7 +939,8 @@ def mixed_block(args, n=None, steps=10, warmup=3):
         # the batch kernel gets handles of its own (compiled concurrently)
         bcodes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
         fb = ex.submit(polar.polar_batch_create, bcodes, True, bshape["threads"],
-                       bshape["smem_stage_max"], bshape["warp_stage_max"], bshape["ctas_per_sm"])
+                       bshape["smem_stage_max"], bshape["warp_stage_max"], bshape["ctas_per_sm"],
+                       bshape.get("flags", 0))
         for f in futs:
             f.result()
         batch = fb.result()
@@ -1044,7 +1046,8 @@ def serve_block(args, loads=(1, 10, 50, 200), seconds=0.5, max_frames=40_000):
     del views
     bshape, bsrc = autotune.batch_shape("f32")
     batch = polar.polar_batch_create(codes, False, bshape["threads"], bshape["smem_stage_max"],
-                                     bshape["warp_stage_max"], bshape["ctas_per_sm"])
+                                     bshape["warp_stage_max"], bshape["ctas_per_sm"],
+                                     bshape.get("flags", 0))
     budget = 4 << 30
     arms = {"served": dict(flags=0, slots=4, max_frames=4096),
             "plain": dict(flags=polar.SERVE_LAUNCH_PER_CODE, slots=1, max_frames=4096)}

@@ -310,6 +310,16 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
                                 const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
                                 polar_batch_t **out);
 
+/* polar_batch_create with a choice of form: flags = 0 inlines every body (as
+ * polar_batch_create); POLAR_COMPILE_OUTLINE_SUBTREES makes each distinct
+ * register subtree one out-of-line function shared by all the codes' bodies
+ * (equal frozen patterns of different codes share code), which makes the
+ * kernel smaller. Other flag bits give POLAR_EINVAL. Same bits either way. */
+polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
+                                   uint32_t threads, const uint32_t *smem_stage_max,
+                                   const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
+                                   uint32_t flags, polar_batch_t **out);
+
 void polar_batch_destroy(polar_batch_t *batch);
 
 /* Decode n_frames frames in one launch on `stream`. All arrays are device

@@ -398,7 +398,19 @@ def tune_batch(tuners, weights=None, sample_frames=16384, workers=6, log=None) -
                 f"(grid {results[-1][2]['grid']})")
         del b
     t, (S, cps), info = min(results, key=lambda r: r[0])
-    return dict(threads=T, smem_stage_max=list(S), warp_stage_max=W0, ctas_per_sm=cps,
+    flags = 0
+    try:  # the same shape with the subtree functions shared by all bodies
+        b = polar.polar_batch_create(codes, tuners[0].dtype == "i8", T, list(S), W0, cps,
+                                     polar.COMPILE_OUTLINE_SUBTREES)
+        t2 = time_batch(b, sample)
+        if log:
+            log(f"  batch T={T} S={list(S)} cps={cps} shared subtrees: {bits / t2 / 1e9:.1f} Gbps")
+        if t2 < t:
+            t, flags = t2, polar.COMPILE_OUTLINE_SUBTREES
+        del b
+    except polar.PolarError:
+        pass
+    return dict(threads=T, smem_stage_max=list(S), warp_stage_max=W0, ctas_per_sm=cps, flags=flags,
                 gbps=bits / t / 1e9, grid=info["grid"], sample_frames=sample_frames,
                 per_code_gbps=[tu.K / tu.best(T)[1] / 1e9 for tu in tuners],
                 expected_s_per_frame={str(k): v for k, v in cost.items()})
@@ -508,8 +520,10 @@ def batch_shape(dtype: str):
         e = None
     if e:
         return dict(threads=e["threads"], smem_stage_max=e["smem_stage_max"],
-                    warp_stage_max=e["warp_stage_max"], ctas_per_sm=e.get("ctas_per_sm", 0)), "tuned"
-    return dict(threads=32, smem_stage_max=None, warp_stage_max=None, ctas_per_sm=0), "default"
+                    warp_stage_max=e["warp_stage_max"], ctas_per_sm=e.get("ctas_per_sm", 0),
+                    flags=e.get("flags", 0)), "tuned"
+    return dict(threads=32, smem_stage_max=None, warp_stage_max=None, ctas_per_sm=0,
+                flags=0), "default"
 
 
 if __name__ == "__main__":

@@ -74,7 +74,16 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
                                 uint32_t threads, const uint32_t *smem_stage_max,
                                 const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
                                 polar_batch_t **out) {
+    return polar_batch_create_ex(codes, n_codes, is_i8, threads, smem_stage_max, warp_stage_max,
+                                 ctas_per_sm, 0, out);
+}
+
+polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
+                                   uint32_t threads, const uint32_t *smem_stage_max,
+                                   const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
+                                   uint32_t flags, polar_batch_t **out) {
     if (!codes || !out || n_codes == 0 || n_codes > 64) return POLAR_EINVAL;
+    if (flags & ~POLAR_COMPILE_OUTLINE_SUBTREES) return POLAR_EINVAL;
     if (threads == 0) threads = 32;
     if (threads % 32 || threads > 1024) return POLAR_EINVAL;
     for (uint32_t c = 0; c < n_codes; ++c) {
@@ -147,8 +156,9 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
                                           size_t(32)});
     if (ctas_per_sm) min_blocks = std::min<size_t>(min_blocks, ctas_per_sm);
     min_blocks = std::max<size_t>(min_blocks, 1);
-    const std::string src = generate_batch_source(cc, b->is_i8, b->S, b->W, b->R, threads,
-                                                  static_cast<uint32_t>(min_blocks));
+    const std::string src = generate_batch_source(
+        cc, b->is_i8, b->S, b->W, b->R, threads, static_cast<uint32_t>(min_blocks),
+        (flags & POLAR_COMPILE_OUTLINE_SUBTREES) ? kOutlineSubtrees : 0u);
     cudaError_t e = compile_source(src, &b->ck, &b->log, "polar_batch");
     if (e != cudaSuccess) {
         const polar_status st = st_of(e);

@@ -236,10 +236,14 @@ size_t emit_reg_ops(std::ostream &o, const std::vector<HostOp> &ops, size_t i, u
 // operations with offsets relative to the subtree, so equal frozen patterns
 // share code), emitted before the body; returns, per list index of a subtree's
 // first operation, the function's id.
+// shared: one id map for several bodies (the mixed-batch kernel), so that equal
+// subtrees of different codes share one function; nullptr for a map of its own.
 std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std::vector<HostOp> &ops,
                                                 const char *T, uint32_t R,
-                                                const std::string &prefix, bool local) {
-    std::map<std::string, size_t> ids;
+                                                const std::string &prefix, bool local,
+                                                std::map<std::string, size_t> *shared = nullptr) {
+    std::map<std::string, size_t> own;
+    std::map<std::string, size_t> &ids = shared ? *shared : own;
     std::map<size_t, size_t> at;
     for (size_t i = 0; i < ops.size(); ++i) {
         if (!(ops[i].flags & OPW_REG_ENTER)) continue;
@@ -250,7 +254,7 @@ std::map<size_t, size_t> emit_subtree_functions(std::ostringstream &o, const std
             j += used;
             if (ops[j - 1].flags & OPW_REG_EXIT) break;
         }
-        const std::string key = std::to_string(n0) + "|" + b.str();
+        const std::string key = std::to_string(n0) + "|" + std::to_string(R) + "|" + b.str();
         auto it = ids.find(key);
         if (it == ids.end()) {
             const size_t id = ids.size();
@@ -313,9 +317,12 @@ std::vector<std::vector<uint32_t>> plan_prefetch(const std::vector<HostOp> &ops,
 // run_warp_frames): every operation is warp-level on the warp's own frame, and
 // a CTA barrier after each register subtree keeps the warps in step.
 // chan_global: the channel LLRs are read in place from device memory.
+// shared_subs: emit register-subtree functions into one map shared with other
+// bodies, named with the prefix "Shared_" (see emit_subtree_functions).
 void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32_t S, uint32_t W,
                uint32_t R, const std::string &name, uint32_t outline = 0,
-               bool warp_frames = false, bool chan_global = true) {
+               bool warp_frames = false, bool chan_global = true,
+               std::map<std::string, size_t> *shared_subs = nullptr) {
     const bool outline_sub = outline & kOutlineSubtrees, outline_mem = outline & kOutlineMemory;
     const bool local = outline & kLocalLeaves;
     const uint32_t N = code.N;
@@ -357,7 +364,8 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     };
     const char *T = is_i8 ? "int8_t" : "float";
     std::map<size_t, size_t> sub_at;
-    if (outline_sub) sub_at = emit_subtree_functions(o, ops, T, R, name + "_", local);
+    const std::string sub_prefix = shared_subs ? std::string("Shared_") : name + "_";
+    if (outline_sub) sub_at = emit_subtree_functions(o, ops, T, R, sub_prefix, local, shared_subs);
     o << "struct " << name << " {\n"
       << "  __device__ __forceinline__ void operator()(const Frame<" << T << "> &fr, float *) const {\n"
       << "    using T = " << T << ";\n"
@@ -515,7 +523,7 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
         for (uint32_t pn : prefetch[i])
             o << "      prefetch_l2(" << in(pn) << ", " << pn * es << "u);\n";
         if (outline_sub && (op.flags & OPW_REG_ENTER)) {  // the whole subtree is one call
-            o << "      " << name << "_sub" << sub_at.at(i) << "(" << in(n) << ", fr.beta, " << op.off
+            o << "      " << sub_prefix << "sub" << sub_at.at(i) << "(" << in(n) << ", fr.beta, " << op.off
               << "u);\n      __syncwarp();\n" << align;
             while (!(ops[i].flags & OPW_REG_EXIT)) ++i;
             continue;
@@ -563,14 +571,16 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
 std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,
                                   const std::vector<uint32_t> &S, const std::vector<uint32_t> &W,
                                   const std::vector<uint32_t> &R, uint32_t threads,
-                                  uint32_t min_blocks) {
+                                  uint32_t min_blocks, uint32_t outline) {
     std::ostringstream o;
     const char *T = is_i8 ? "int8_t" : "float";
     o << "// Mixed-batch Fast-SSC decoder: one specialised body per code\n"
       << "#include \"polar_ops.cuh\"\n"
       << "namespace polar {\n";
+    std::map<std::string, size_t> shared;  // subtree functions common to every body
     for (size_t c = 0; c < codes.size(); ++c)
-        emit_body(o, *codes[c], is_i8, S[c], W[c], R[c], "Body" + std::to_string(c));
+        emit_body(o, *codes[c], is_i8, S[c], W[c], R[c], "Body" + std::to_string(c), outline,
+                  false, true, &shared);
     o << "struct BatchBody {\n"
       << "  __device__ __forceinline__ void operator()(uint32_t cid, const Frame<" << T
       << "> &fr) const {\n    switch (cid) {\n";

@@ -282,11 +282,12 @@ constexpr uint32_t kLocalLeaves = 4u;
 std::string generate_source(const polar_code &code, bool is_i8, const LaunchShape &shape,
                             uint32_t reg_subtree, uint32_t outline = 0);
 // Source of the mixed-batch decoder: one specialised body per code (per-code
-// shared-memory stage cap S, warp threshold W, register subtree R).
+// shared-memory stage cap S, warp threshold W, register subtree R); outline as
+// for generate_source, with the subtree functions shared by all bodies.
 std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,
                                   const std::vector<uint32_t> &S, const std::vector<uint32_t> &W,
                                   const std::vector<uint32_t> &R, uint32_t threads,
-                                  uint32_t min_blocks);
+                                  uint32_t min_blocks, uint32_t outline = 0);
 // Compile generated source with NVRTC for the current device's architecture and
 // load `kernel_name` from it. Returns cudaSuccess and fills *out, or an error
 // (log in *log).

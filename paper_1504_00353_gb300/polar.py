@@ -26,7 +26,8 @@ EXPORTS = [
     "polar_decode_i8", "polar_code_trace_len", "polar_decode_trace", "polar_code_set_launch",
     "polar_code_get_launch", "polar_code_check", "polar_code_compile", "polar_code_compile_ex",
     "polar_code_compile_log",
-    "polar_decode_noalloc", "polar_batch_create", "polar_batch_destroy", "polar_batch_decode",
+    "polar_decode_noalloc", "polar_batch_create", "polar_batch_create_ex", "polar_batch_destroy",
+    "polar_batch_decode",
     "polar_batch_info", "polar_batch_log", "polar_server_create", "polar_server_publish",
     "polar_server_progress", "polar_server_destroy", "polar_random_info",
     "polar_encode_systematic_device", "polar_channel_awgn", "polar_count_errors", "polar_fer_run",
@@ -75,6 +76,8 @@ def _load():
         "polar_code_compile_log": ([vp], ctypes.c_char_p),
         "polar_code_check": ([vp, vp], st),
         "polar_batch_create": ([ctypes.POINTER(vp), u32, st, u32, u32p, u32p, u32,
+                                ctypes.POINTER(vp)], st),
+        "polar_batch_create_ex": ([ctypes.POINTER(vp), u32, st, u32, u32p, u32p, u32, u32,
                                 ctypes.POINTER(vp)], st),
         "polar_batch_destroy": ([vp], None),
         "polar_batch_decode": ([vp, vp, vp, vp, vp, vp, sz, vp], st),
@@ -371,7 +374,7 @@ class PolarBatch:
 
 
 def polar_batch_create(codes, is_i8: bool, threads: int = 0, smem_stage_max=None,
-                       warp_stage_max=None, ctas_per_sm: int = 0) -> PolarBatch:
+                       warp_stage_max=None, ctas_per_sm: int = 0, flags: int = 0) -> PolarBatch:
     """One persistent decoder for frames of any of `codes`; per-code shared-memory
     stage cap and warp threshold (lists, 0 = default)."""
     arr = (ctypes.c_void_p * len(codes))(*[c.handle.value for c in codes])
@@ -380,9 +383,9 @@ def polar_batch_create(codes, is_i8: bool, threads: int = 0, smem_stage_max=None
         return None if v is None else (ctypes.c_uint32 * len(codes))(*[int(x) for x in v])
 
     h = ctypes.c_void_p()
-    st = _lib.polar_batch_create(arr, len(codes), int(bool(is_i8)), threads,
-                                 per_code(smem_stage_max), per_code(warp_stage_max), ctas_per_sm,
-                                 ctypes.byref(h))
+    st = _lib.polar_batch_create_ex(arr, len(codes), int(bool(is_i8)), threads,
+                                    per_code(smem_stage_max), per_code(warp_stage_max), ctas_per_sm,
+                                    flags, ctypes.byref(h))
     if st != 0:
         raise PolarError(st, "polar_batch_create: " +
                          (_lib.polar_batch_log(None) or b"").decode(errors="replace")[-3000:])

@@ -48,11 +48,15 @@ def check(masks, cid, llrs, got, oo):
         assert np.array_equal(got[oo[i]: oo[i] + (K + 7) // 8], want), (i, c)
 
 
-@pytest.mark.parametrize("i8,threads", [(True, 32), (False, 32), (True, 128)])
-def test_mixed_batch_matches_oracle(i8, threads):
+@pytest.mark.parametrize("i8,threads,flags", [(True, 32, 0), (False, 32, 0), (True, 128, 0),
+                                              (True, 32, polar.COMPILE_OUTLINE_SUBTREES),
+                                              (False, 128, polar.COMPILE_OUTLINE_SUBTREES)])
+def test_mixed_batch_matches_oracle(i8, threads, flags):
+    """Every frame's bits equal the oracle's, for the inlined bodies and for
+    bodies sharing one function per distinct register subtree across codes."""
     masks, cid, llrs, lo, oo, total_out = mixed_frames(300, 50 + threads, i8)
     codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(CODES, masks)]
-    batch = polar.polar_batch_create(codes, i8, threads)
+    batch = polar.polar_batch_create(codes, i8, threads, flags=flags)
     assert polar.polar_batch_info(batch)["grid"] > 0
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     llr = dev(np.concatenate(llrs))

@@ -104,7 +104,7 @@ def test_mixed_batch_tuned_shape(dtype):
     codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(nk, masks)]
     batch = polar.polar_batch_create(codes, dtype == "i8", shape["threads"],
                                      shape["smem_stage_max"], shape["warp_stage_max"],
-                                     shape["ctas_per_sm"])
+                                     shape["ctas_per_sm"], shape.get("flags", 0))
     info = polar.polar_batch_info(batch)
     assert info["grid"] > 0
     rng = np.random.default_rng(93)
