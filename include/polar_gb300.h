@@ -314,7 +314,14 @@ polar_status polar_batch_create(polar_code_t *const *codes, uint32_t n_codes, in
  * polar_batch_create); POLAR_COMPILE_OUTLINE_SUBTREES makes each distinct
  * register subtree one out-of-line function shared by all the codes' bodies
  * (equal frozen patterns of different codes share code), which makes the
- * kernel smaller. Other flag bits give POLAR_EINVAL. Same bits either way. */
+ * kernel smaller. POLAR_BATCH_FRAME_PER_WARP with threads = 32 x F (F = 2..8)
+ * decodes F frames per CTA, one per warp: the CTA claims F consecutive frames
+ * of the list and its warps run the frames' code body side by side (when the
+ * F frames are of several codes, each code's body in turn); warp thresholds
+ * then do not apply (every operation is warp-level) and per-code stage caps
+ * size one shared-memory slot per warp. Other flag bits give POLAR_EINVAL.
+ * Same bits in every form. */
+#define POLAR_BATCH_FRAME_PER_WARP 16u
 polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes, int is_i8,
                                    uint32_t threads, const uint32_t *smem_stage_max,
                                    const uint32_t *warp_stage_max, uint32_t ctas_per_sm,

@@ -398,19 +398,27 @@ def tune_batch(tuners, weights=None, sample_frames=16384, workers=6, log=None) -
                 f"(grid {results[-1][2]['grid']})")
         del b
     t, (S, cps), info = min(results, key=lambda r: r[0])
-    flags = 0
-    try:  # the same shape with the subtree functions shared by all bodies
-        b = polar.polar_batch_create(codes, tuners[0].dtype == "i8", T, list(S), W0, cps,
-                                     polar.COMPILE_OUTLINE_SUBTREES)
+    flags, threads = 0, T
+    # the same stage caps with subtree functions shared by all bodies, and (one
+    # warp per frame) with two or four frames per CTA
+    trials = [(T, polar.COMPILE_OUTLINE_SUBTREES, cps)]
+    if T == 32:
+        trials += [(32 * f, polar.BATCH_FRAME_PER_WARP, (cps + f - 1) // f if cps else 0)
+                   for f in (2, 4)]
+    for tt, fl, cc in trials:
+        try:
+            b = polar.polar_batch_create(codes, tuners[0].dtype == "i8", tt, list(S), W0, cc, fl)
+        except polar.PolarError:
+            continue
         t2 = time_batch(b, sample)
         if log:
-            log(f"  batch T={T} S={list(S)} cps={cps} shared subtrees: {bits / t2 / 1e9:.1f} Gbps")
+            log(f"  batch T={tt} S={list(S)} cps={cc} flags={fl}: {bits / t2 / 1e9:.1f} Gbps")
         if t2 < t:
-            t, flags = t2, polar.COMPILE_OUTLINE_SUBTREES
+            t, flags, threads, cps = t2, fl, tt, cc
+            info = polar.polar_batch_info(b)
         del b
-    except polar.PolarError:
-        pass
-    return dict(threads=T, smem_stage_max=list(S), warp_stage_max=W0, ctas_per_sm=cps, flags=flags,
+    return dict(threads=threads, smem_stage_max=list(S), warp_stage_max=W0, ctas_per_sm=cps,
+                flags=flags,
                 gbps=bits / t / 1e9, grid=info["grid"], sample_frames=sample_frames,
                 per_code_gbps=[tu.K / tu.best(T)[1] / 1e9 for tu in tuners],
                 expected_s_per_frame={str(k): v for k, v in cost.items()})

@@ -62,7 +62,7 @@ cudaError_t batch_launch(polar_batch *b, const uint32_t *code_id, const uint64_t
     a.smem_alpha_elems = b->alpha_elems;
     a.smem_beta_words = b->beta_words;
     LaunchShape sh = b->shape;
-    sh.grid = static_cast<uint32_t>(std::min<size_t>(sh.grid, n_frames));
+    sh.grid = static_cast<uint32_t>(b->grid_for(n_frames));
     return launch_compiled(&b->ck, sh, &a, stream);
 }
 
@@ -83,9 +83,11 @@ polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes,
                                    const uint32_t *warp_stage_max, uint32_t ctas_per_sm,
                                    uint32_t flags, polar_batch_t **out) {
     if (!codes || !out || n_codes == 0 || n_codes > 64) return POLAR_EINVAL;
-    if (flags & ~POLAR_COMPILE_OUTLINE_SUBTREES) return POLAR_EINVAL;
+    if (flags & ~(POLAR_COMPILE_OUTLINE_SUBTREES | POLAR_BATCH_FRAME_PER_WARP)) return POLAR_EINVAL;
     if (threads == 0) threads = 32;
     if (threads % 32 || threads > 1024) return POLAR_EINVAL;
+    const bool warp_frames = (flags & POLAR_BATCH_FRAME_PER_WARP) && threads > 32;
+    if (warp_frames && threads > 32 * 8) return POLAR_EINVAL;  // at most 8 frames per CTA
     for (uint32_t c = 0; c < n_codes; ++c) {
         if (!codes[c]) return POLAR_EINVAL;
         if (smem_stage_max && smem_stage_max[c] && !is_pow2(smem_stage_max[c])) return POLAR_EINVAL;
@@ -101,6 +103,7 @@ polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes,
     b->is_i8 = is_i8 != 0;
     b->device = device;
     b->threads = threads;
+    b->frames_per_cta = warp_frames ? threads / 32 : 1;
     const size_t es = b->elem_bytes();
     constexpr uint32_t kReg = 256;  // register-resident subtree size of every body
     std::vector<CodeDesc> desc(n_codes);
@@ -141,8 +144,11 @@ polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes,
         desc[c].out_row = (code->K + 7) / 8;
         desc[c].S = b->S[c];
     }
-    const size_t smem = align_up(size_t(b->alpha_elems) * es, 128) +
-                        align_up(size_t(b->beta_words) * 4, 16) + 32 * 8 + 32 * 4;
+    const size_t smem =
+        warp_frames ? b->frames_per_cta * batch_slot_bytes(b->alpha_elems, b->beta_words,
+                                                           static_cast<uint32_t>(es))
+                    : align_up(size_t(b->alpha_elems) * es, 128) +
+                          align_up(size_t(b->beta_words) * 4, 16) + 32 * 8 + 32 * 4;
     int optin = 0, sms = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -158,7 +164,7 @@ polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes,
     min_blocks = std::max<size_t>(min_blocks, 1);
     const std::string src = generate_batch_source(
         cc, b->is_i8, b->S, b->W, b->R, threads, static_cast<uint32_t>(min_blocks),
-        (flags & POLAR_COMPILE_OUTLINE_SUBTREES) ? kOutlineSubtrees : 0u);
+        (flags & POLAR_COMPILE_OUTLINE_SUBTREES) ? kOutlineSubtrees : 0u, warp_frames);
     cudaError_t e = compile_source(src, &b->ck, &b->log, "polar_batch");
     if (e != cudaSuccess) {
         const polar_status st = st_of(e);
@@ -184,7 +190,7 @@ polar_status polar_batch_create_ex(polar_code_t *const *codes, uint32_t n_codes,
         e = cudaMemcpy(b->d_codes, desc.data(), sizeof(CodeDesc) * n_codes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned int));
     if (e == cudaSuccess && b->gstride)
-        e = cudaMalloc(&b->scratch, b->scratch_bytes(b->shape.grid));
+        e = cudaMalloc(&b->scratch, b->scratch_bytes(size_t(b->shape.grid) * b->frames_per_cta));
     if (e != cudaSuccess) {
         const polar_status st = st_of(e);
         delete b;
@@ -219,7 +225,7 @@ polar_status polar_batch_info(const polar_batch_t *b, uint32_t *threads, uint32_
     if (threads) *threads = b->shape.threads;
     if (grid) *grid = b->shape.grid;
     if (smem_bytes) *smem_bytes = b->shape.smem_bytes;
-    if (scratch_bytes) *scratch_bytes = b->scratch_bytes(b->shape.grid);
+    if (scratch_bytes) *scratch_bytes = b->scratch_bytes(size_t(b->shape.grid) * b->frames_per_cta);
     return POLAR_OK;
 }
 

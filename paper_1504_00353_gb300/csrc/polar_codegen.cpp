@@ -571,7 +571,7 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
 std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,
                                   const std::vector<uint32_t> &S, const std::vector<uint32_t> &W,
                                   const std::vector<uint32_t> &R, uint32_t threads,
-                                  uint32_t min_blocks, uint32_t outline) {
+                                  uint32_t min_blocks, uint32_t outline, bool warp_frames) {
     std::ostringstream o;
     const char *T = is_i8 ? "int8_t" : "float";
     o << "// Mixed-batch Fast-SSC decoder: one specialised body per code\n"
@@ -580,7 +580,7 @@ std::string generate_batch_source(const std::vector<const polar_code *> &codes, 
     std::map<std::string, size_t> shared;  // subtree functions common to every body
     for (size_t c = 0; c < codes.size(); ++c)
         emit_body(o, *codes[c], is_i8, S[c], W[c], R[c], "Body" + std::to_string(c), outline,
-                  false, true, &shared);
+                  warp_frames, true, &shared);
     o << "struct BatchBody {\n"
       << "  __device__ __forceinline__ void operator()(uint32_t cid, const Frame<" << T
       << "> &fr) const {\n    switch (cid) {\n";
@@ -589,7 +589,8 @@ std::string generate_batch_source(const std::vector<const polar_code *> &codes, 
     o << "    default: break;\n    }\n  }\n};\n}  // namespace polar\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
       << std::max<uint32_t>(min_blocks, 1) << ") polar_batch(const polar::BatchArgs a) {\n"
-      << "  polar::run_batch<" << T << ">(a, polar::BatchBody{});\n}\n";
+      << "  polar::" << (warp_frames ? "run_batch_warps<" : "run_batch<") << T
+      << ">(a, polar::BatchBody{});\n}\n";
     return o.str();
 }
 

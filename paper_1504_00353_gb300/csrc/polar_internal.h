@@ -255,15 +255,20 @@ struct polar_batch {
     polar::CodeDesc *d_codes = nullptr;
     unsigned int *d_counter = nullptr;
     void *scratch = nullptr;
-    size_t gstride = 0;  // scratch elements per CTA
+    size_t gstride = 0;  // scratch elements per frame slot
     uint32_t alpha_elems = 0, beta_words = 0;
+    uint32_t frames_per_cta = 1;  // > 1: one frame per warp (POLAR_BATCH_FRAME_PER_WARP)
     std::string log;
 
     size_t elem_bytes() const { return is_i8 ? 1 : 4; }
+    // CTAs one launch over n_frames frames uses.
+    size_t grid_for(size_t n_frames) const {
+        const size_t groups = (n_frames + frames_per_cta - 1) / frames_per_cta;
+        return groups < shape.grid ? groups : shape.grid;
+    }
     // Scratch bytes one launch over n_frames frames needs.
     size_t scratch_bytes(size_t n_frames) const {
-        const size_t g = n_frames < shape.grid ? n_frames : shape.grid;
-        return g * gstride * elem_bytes();
+        return grid_for(n_frames) * frames_per_cta * gstride * elem_bytes();
     }
     ~polar_batch();
 };
@@ -287,7 +292,8 @@ std::string generate_source(const polar_code &code, bool is_i8, const LaunchShap
 std::string generate_batch_source(const std::vector<const polar_code *> &codes, bool is_i8,
                                   const std::vector<uint32_t> &S, const std::vector<uint32_t> &W,
                                   const std::vector<uint32_t> &R, uint32_t threads,
-                                  uint32_t min_blocks, uint32_t outline = 0);
+                                  uint32_t min_blocks, uint32_t outline = 0,
+                                  bool warp_frames = false);
 // Compile generated source with NVRTC for the current device's architecture and
 // load `kernel_name` from it. Returns cudaSuccess and fills *out, or an error
 // (log in *log).

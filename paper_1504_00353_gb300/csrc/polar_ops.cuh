@@ -98,6 +98,8 @@ struct KernelArgs {
     uint32_t out_row;              // bytes per output row (ceil(K/8))
 };
 
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
 // One code of a mixed batch, as the batch kernel sees it.
 struct CodeDesc {
     const uint32_t *ext_mask;      // as in KernelArgs
@@ -119,13 +121,21 @@ struct BatchArgs {
     uint8_t *out;
     unsigned int *counter;         // next unclaimed frame; zero before the launch
     void *gscratch;
-    size_t gstride;                // scratch elements per CTA (max over codes)
+    size_t gstride;                // scratch elements per frame slot (max over codes)
     size_t n_frames;
     uint32_t smem_alpha_elems;     // alpha region: max over codes of 2 * S
     uint32_t smem_beta_words;      // beta region: max over codes of NW
 };
 
-__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+// Shared-memory bytes of one frame slot of the batch kernel (alpha, beta,
+// reduction slots), computed identically on host and device.
+__host__ __device__ inline size_t batch_slot_bytes(uint32_t alpha_elems, uint32_t beta_words,
+                                                   uint32_t es) {
+    return align_up(align_up(size_t(alpha_elems) * es, 128) + align_up(size_t(beta_words) * 4, 16) +
+                        32 * 8 + 32 * 4,
+                    128);
+}
+
 
 // Shared-memory carve-up, computed identically on host and device.
 struct SmemLayout {
@@ -1058,6 +1068,80 @@ __device__ __forceinline__ void run_batch(const BatchArgs &a, const Body &body) 
             for (uint32_t b = 0; b < nb; ++b) out[4u * u + b] = static_cast<uint8_t>(acc >> (8 * b));
         }
         __syncthreads();
+    }
+}
+
+// Persistent loop of the mixed-batch kernel with several frames per CTA, one
+// per warp: the CTA claims F = blockDim.x / 32 consecutive frames of the list
+// (listed longest code first, so they are almost always frames of one code)
+// and its warps run that code's body side by side, each on its own frame,
+// shared-memory slot and scratch slot, meeting at the CTA barriers the
+// warp-level bodies place after each register subtree. When the F frames
+// belong to several codes, the CTA runs the body of each of those codes in
+// turn; in a turn, a warp whose frame is of another code decodes a copy of the
+// turn's first frame of that code and stores nothing, so that every warp passes
+// the same barriers. The same holds for the warps past the end of the list.
+template <typename T, class Body>
+__device__ __forceinline__ void run_batch_warps(const BatchArgs &a, const Body &body) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned int s_base;
+    __shared__ uint32_t s_cid[32];
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5, F = blockDim.x >> 5;
+    const size_t slot = batch_slot_bytes(a.smem_alpha_elems, a.smem_beta_words, sizeof(T));
+    unsigned char *base = smem + size_t(w) * slot;
+    const size_t alpha_bytes = align_up(size_t(a.smem_alpha_elems) * sizeof(T), 128);
+    const size_t beta_bytes = align_up(size_t(a.smem_beta_words) * 4, 16);
+    Frame<T> fr;
+    fr.s_alpha = reinterpret_cast<T *>(base);
+    fr.beta = reinterpret_cast<uint32_t *>(base + alpha_bytes);
+    fr.rkey = reinterpret_cast<unsigned long long *>(base + alpha_bytes + beta_bytes);
+    fr.rpar = reinterpret_cast<uint32_t *>(base + alpha_bytes + beta_bytes + 32 * 8);
+    fr.g_alpha = a.gscratch ? static_cast<T *>(a.gscratch) + (size_t(blockIdx.x) * F + w) * a.gstride
+                            : nullptr;
+    const T *llr = static_cast<const T *>(a.llr);
+    for (;;) {
+        if (threadIdx.x == 0) s_base = atomicAdd(a.counter, F);
+        __syncthreads();
+        const size_t first = s_base;
+        if (first >= a.n_frames) break;
+        const size_t item = first + w;
+        if (lane == 0) s_cid[w] = __ldg(a.code_id + (item < a.n_frames ? item : first));
+        __syncthreads();
+        const uint32_t mine = s_cid[w];
+        for (uint32_t k = 0; k < F; ++k) {
+            const uint32_t cid = s_cid[k];
+            bool seen = false;
+            for (uint32_t j = 0; j < k; ++j) seen |= s_cid[j] == cid;
+            if (seen) continue;  // this code's turn has been run
+            const bool own = mine == cid && item < a.n_frames;
+            const size_t src = own ? item : first + k;
+            const CodeDesc d = a.codes[cid];
+            fr.N = d.N;
+            fr.S = d.S;
+            fr.chan = llr + __ldg(a.llr_off + src);
+            body(cid, fr);
+            if (own) {
+                uint8_t *out = a.out + __ldg(a.out_off + item);
+                for (uint32_t u = lane; u < d.KW; u += 32u) {
+                    const uint32_t lo = u << 5;
+                    const uint32_t hi = min(lo + 32u, d.K);
+                    uint32_t acc = 0;
+                    for (uint32_t wd = __ldg(d.ext_wstart + u); wd < d.NW; ++wd) {
+                        const uint32_t pre = __ldg(d.ext_pre + wd);
+                        if (pre >= hi) break;
+                        const uint32_t m = __ldg(d.ext_mask + wd);
+                        if (!m) continue;
+                        const uint32_t e = pext32(fr.beta[wd], m);
+                        const int pos = static_cast<int>(pre) - static_cast<int>(lo);
+                        acc |= pos >= 0 ? (e << pos) : (e >> (-pos));
+                    }
+                    if (hi - lo < 32) acc &= (1u << (hi - lo)) - 1u;
+                    const uint32_t nb = min(4u, d.out_row - 4u * u);
+                    for (uint32_t b = 0; b < nb; ++b) out[4u * u + b] = static_cast<uint8_t>(acc >> (8 * b));
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 

@@ -326,6 +326,7 @@ def polar_code_set_frames_per_cta(code: PolarCode, is_i8: bool, frames: int):
 
 COMPILE_OUTLINE_SUBTREES, COMPILE_OUTLINE_MEMORY, COMPILE_COMPACT, COMPILE_FULL = 1, 2, 3, 4
 COMPILE_LOCAL_LEAVES = 8
+BATCH_FRAME_PER_WARP = 16
 
 
 def polar_code_compile(code: PolarCode, is_i8: bool, n_frames: int, reg_subtree: int = 0,

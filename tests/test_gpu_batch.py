@@ -147,3 +147,31 @@ def test_batch_rejects_oversized_frame_count():
     z = torch.zeros(16, dtype=torch.int64, device="cuda")
     with pytest.raises(polar.PolarError):
         polar.polar_batch_decode(batch, z, z, z, z, z.to(torch.uint8), n_frames=1 << 32)
+
+
+@pytest.mark.parametrize("i8,F,flags,shuffled", [(True, 4, 0, False), (False, 2, 0, True),
+                                                 (True, 4, 0, True),
+                                                 (True, 2, polar.COMPILE_OUTLINE_SUBTREES, False)])
+def test_mixed_batch_frame_per_warp(i8, F, flags, shuffled):
+    """Several frames per CTA, one per warp: the CTA's warps decode consecutive
+    frames of the list side by side. Frames in arrival order (shuffled) put
+    frames of different codes in most groups, which the CTA then decodes code by
+    code; 301 frames leave a ragged last group. Every frame equals the oracle."""
+    masks, cid, llrs, lo, oo, total_out = mixed_frames(301, 70 + F + 10 * shuffled, i8)
+    if shuffled:
+        perm = np.random.default_rng(5).permutation(cid.size)
+        cid, lo, oo = cid[perm], lo[perm], oo[perm]
+        llrs = [llrs[i] for i in perm]
+        # re-lay the LLR and output buffers in the new order
+        lo = np.concatenate([[0], np.cumsum([CODES[c][0] for c in cid])[:-1]]).astype(np.uint64)
+        oo = np.concatenate([[0], np.cumsum([(CODES[c][1] + 7) // 8 for c in cid])[:-1]]).astype(np.uint64)
+    codes = [polar.polar_code_create(N, K, m) for (N, K), m in zip(CODES, masks)]
+    batch = polar.polar_batch_create(codes, i8, 32 * F, flags=flags | polar.BATCH_FRAME_PER_WARP)
+    assert polar.polar_batch_info(batch)["threads"] == 32 * F
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    llr = dev(np.concatenate(llrs))
+    out = torch.full((total_out,), 0xA5, dtype=torch.uint8, device="cuda")
+    polar.polar_batch_decode(batch, dev(cid.view(np.int32)), dev(lo.view(np.int64)),
+                             dev(oo.view(np.int64)), llr, out)
+    torch.cuda.synchronize()
+    check(masks, cid, llrs, out.cpu().numpy(), oo)
