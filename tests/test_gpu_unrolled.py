@@ -229,7 +229,7 @@ def test_frames_per_cta_memory_level_nodes(F):
 
 
 @pytest.mark.parametrize("i8", [False, True])
-@pytest.mark.parametrize("N,reg", [(64, 64), (1024, 256), (4096, 1024)])
+@pytest.mark.parametrize("N,reg", [(64, 64), (1024, 256), (2048, 512)])
 def test_local_leaves_random_masks(i8, N, reg):
     """The per-lane form of split nodes of 4 to 16 leaves (every lane decodes
     the node on its own) gives the oracle's bits on random masks, including
