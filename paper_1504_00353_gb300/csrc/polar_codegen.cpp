@@ -448,17 +448,21 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
         }
     };
 
-    // Memory-resident F/G/G_0R operation i followed by up to two operations
-    // that each read the stage the previous one wrote (the first operation of
-    // the node it produced LLRs for: F or G_0R): emitted as one fused op_chain
-    // when the last stage holds at least one vector per column. Returns the
-    // number of operations covered (1 = not fused).
+    // Memory-resident F/G/G_0R operation i followed by up to max_chain - 1
+    // operations that each read the stage the previous one wrote (the first
+    // operation of the node it produced LLRs for: F or G_0R): emitted as one
+    // fused op_chain when the last stage holds at least one vector per column.
+    // Returns the number of operations covered (1 = not fused). int8 chains stop
+    // at two operations: three hold 56 registers of 16-byte vectors and measured
+    // slower under the 72-register budget of the int8 decoder (more local
+    // memory); float32 chains go to three.
     const uint32_t vec = is_i8 ? 16u : 4u;
+    const uint32_t max_chain = is_i8 ? 2u : 3u;
     auto chain_len = [&](size_t i) -> uint32_t {
         const HostOp &a = ops[i];
         if ((a.flags & OPW_REG) || a.kind > OP_G0R) return 1;
         uint32_t len = 1;
-        for (size_t j = i; len < 3 && j + 1 < ops.size(); ++j, ++len) {
+        for (size_t j = i; len < max_chain && j + 1 < ops.size(); ++j, ++len) {
             const HostOp &p = ops[j], &q = ops[j + 1];
             const uint32_t pn = 1u << p.log2n;
             const uint32_t child_off = p.kind == OP_F ? p.off : p.off + pn / 2;
