@@ -206,15 +206,36 @@ def profile_traffic(workload, dtype):
     return float(m.group(1))
 
 
-def profile_smem(workload, dtype):
-    """Shared-memory bytes per launch (ncu smsp__sass_data_bytes_mem_shared.sum)
-    from the committed summary of the specialised decoder, under the same
-    source-hash rule as profile_traffic."""
+def profile_value(workload, dtype, key):
+    """A `key: value` figure from the committed ncu summary of the specialised
+    decoder, under the same source-hash rule as profile_traffic."""
     path = os.path.join(ROOT, "profiles", f"fastssc_unrolled_{dtype}_{workload}.md")
     if not os.path.exists(path) or profile_traffic(workload, dtype) is None:
         return None
-    m = re.search(r"smem_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
+    m = re.search(rf"^{re.escape(key)}:\s*([0-9.eE+]+)", open(path).read(), re.M)
     return float(m.group(1)) if m else None
+
+
+def profile_smem(workload, dtype):
+    """Shared-memory bytes per launch (ncu smsp__sass_data_bytes_mem_shared.sum)."""
+    return profile_value(workload, dtype, "smem_bytes_per_launch")
+
+
+def profile_pipes(workload, dtype, element_ops):
+    """Pipe and issue-slot utilisation of the decoder (ncu, percent of peak
+    sustained over active cycles, as fractions) and thread instructions per
+    element operation, from the committed summary; None when absent or stale."""
+    keys = {"alu": "alu_pipe_busy", "fma": "fma_pipe_busy", "lsu": "lsu_pipe_busy",
+            "issue": "issue_slots_busy"}
+    out = {k: profile_value(workload, dtype, v) for k, v in keys.items()}
+    if any(v is None for v in out.values()):
+        return None
+    tie = profile_value(workload, dtype, "thread_inst_per_launch")
+    out["thread_inst_per_element_op"] = None if tie is None or not element_ops else tie / element_ops
+    out["source"] = ("ncu sm__inst_executed_pipe_{alu,fma,lsu} and smsp__issue_active "
+                     "(pct_of_peak_sustained_active) and thread_inst_executed_true of the "
+                     "committed profile")
+    return out
 
 
 def peaks():
@@ -602,6 +623,7 @@ def run_native(args, world, rank, local):
                          "frac": smem / (r["launch_ms"] * 1e-3) / smem_peak,
                          "source": "ncu smsp__sass_data_bytes_mem_shared.sum of the committed "
                                    "profile; peak = SMs x 128 B/clk x maximum SM clock"},
+                     "pipes": profile_pipes(args.workload, main, ops),
                      "launch_ms": r["launch_ms"]},
         "clocks": clocks,
     }
