@@ -202,39 +202,92 @@ __device__ __forceinline__ int op_add(int a, int b) { return sat127(a + b); }
 __device__ __forceinline__ uint32_t mag_bits(float a) { return __float_as_uint(fabsf(a)); }
 __device__ __forceinline__ uint32_t mag_bits(int a) { return static_cast<uint32_t>(abs(a)); }
 
-// Four int8 lanes per 32-bit word.
-__device__ __forceinline__ uint32_t bytes_from_bits4(uint32_t bits4) {
-    return ((bits4 * 0x00204081u) & 0x01010101u) * 0xFFu;  // bit k -> byte k = 0xFF
-}
-// 0xFF in every byte of x whose sign bit is set (prmt's sign-replicating byte
-// selectors 8..B), 0x00 elsewhere.
-__device__ __forceinline__ uint32_t sign_bytes(uint32_t x) {
+// Four int8 lanes per 32-bit word, computed as two f16x2 pairs. Every int8
+// value and every sum of two of them is an integer of magnitude <= 254, exact
+// in f16, so F (one min.xorsign.abs, Eq. 1), G and G_0R (one IEEE add, Eq. 2,
+// then the clamp to [-127, 127] that the saturating byte add followed by
+// max(-127) gives) are exact: the results are the byte results bit for bit.
+// The arithmetic runs on the FP16 units instead of byte-wise integer sequences.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t r;
-    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(x));
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
     return r;
 }
-// Eq. 1 on four bytes in [-127, 127]. Per byte: |a| = (a ^ s) + (s & 1) with s
-// the sign mask (no carry leaves a byte: the sum is at most 127); |a| >= |b| is
-// bit 7 of (|a| | 0x80) - |b| (no borrow leaves a byte: the difference is at
-// least 1); the magnitude m is negated where the signs differ as
-// (0x80 - m) ^ 0x80, which maps 0 to 0 and stays inside the byte.
-__device__ __forceinline__ uint32_t f_i8x4(uint32_t a, uint32_t b) {
-    const uint32_t sa = sign_bytes(a), sb = sign_bytes(b);
-    const uint32_t ma = (a ^ sa) + (sa & 0x01010101u);
-    const uint32_t mb = (b ^ sb) + (sb & 0x01010101u);
-    const uint32_t ge = sign_bytes((ma | 0x80808080u) - mb);
-    const uint32_t m = (mb & ge) | (ma & ~ge);
-    const uint32_t ns = sa ^ sb;
-    const uint32_t neg = (0x80808080u - m) ^ 0x80808080u;
-    return (neg & ns) | (m & ~ns);
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
 }
-__device__ __forceinline__ uint32_t g_i8x4(uint32_t a, uint32_t b, uint32_t bits4) {
-    const uint32_t sel = bytes_from_bits4(bits4);
-    const uint32_t an = (a & ~sel) | (__vneg4(a) & sel);
-    return __vmaxs4(__vaddss4(b, an), 0x81818181u);
+__device__ __forceinline__ uint32_t hmin2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
 }
-__device__ __forceinline__ uint32_t g0r_i8x4(uint32_t a, uint32_t b) {
-    return __vmaxs4(__vaddss4(b, a), 0x81818181u);
+__device__ __forceinline__ uint32_t hmax2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("max.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// Eq. 1 on two f16 lanes: min(|a|, |b|) carrying the XOR of the signs.
+__device__ __forceinline__ uint32_t hf2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// Clamp both f16 lanes to [-127, 127] (0xD7F0 = -127, 0x57F0 = 127).
+__device__ __forceinline__ uint32_t hsat2(uint32_t v) {
+    return hmin2(hmax2(v, 0xD7F0D7F0u), 0x57F057F0u);
+}
+
+// Four int8 LLRs as two f16x2 words: bytes 0, 1 in lo, bytes 2, 3 in hi.
+struct H4 {
+    uint32_t lo, hi;
+};
+// Byte x (in [-127, 127]) flipped to x + 128 = x ^ 0x80 under the exponent
+// byte 0x64 is the f16 1024 + x + 128 (f16 steps by 1 in [1024, 2048)); adding
+// -1152 (0xE480) leaves x exactly.
+__device__ __forceinline__ H4 h4_unpack(uint32_t w) {
+    const uint32_t u = w ^ 0x80808080u;
+    return {hadd2(prmt(u, 0x64646464u, 0x4140u), 0xE480E480u),
+            hadd2(prmt(u, 0x64646464u, 0x4342u), 0xE480E480u)};
+}
+// Back to bytes: for an integer x in [-254, 254], 1280 + x (0x6500 = 1280) lies
+// in [1024, 2048), so its mantissa is 256 + x, whose low byte is x mod 256: the
+// two's-complement byte. (-0 maps to 0.)
+__device__ __forceinline__ uint32_t h4_pack(H4 v) {
+    return prmt(hadd2(v.lo, 0x65006500u), hadd2(v.hi, 0x65006500u), 0x6420u);
+}
+// F / G / G_0R on four LLRs; bits4 = beta_l of the four (bit k for element k).
+// G flips the sign of alpha_v[i] where beta_l is 1 (Listing 3's sign XOR): the
+// sign bits of elements 0..3 sit at bits 15, 31 of lo and of hi, and bit k of
+// bits4 reaches them by one multiply (the partial products land on disjoint
+// bits, so nothing carries).
+template <uint32_t KIND>
+__device__ __forceinline__ H4 h4_op(H4 a, H4 b, uint32_t bits4) {
+    if constexpr (KIND == OP_F) {
+        return {hf2(a.lo, b.lo), hf2(a.hi, b.hi)};
+    } else if constexpr (KIND == OP_G) {
+        const uint32_t ml = (bits4 * 0x40008000u) & 0x80008000u;
+        const uint32_t mh = (bits4 * 0x10002000u) & 0x80008000u;
+        return {hsat2(hadd2(b.lo, a.lo ^ ml)), hsat2(hadd2(b.hi, a.hi ^ mh))};
+    } else {
+        return {hsat2(hadd2(b.lo, a.lo)), hsat2(hadd2(b.hi, a.hi))};
+    }
+}
+template <uint32_t KIND>
+__device__ __forceinline__ uint32_t op_i8x4(uint32_t a, uint32_t b, uint32_t bits4) {
+    return h4_pack(h4_op<KIND>(h4_unpack(a), h4_unpack(b), bits4));
+}
+
+// 32-bit word j of a 16-byte vector (j a constant after unrolling).
+__device__ __forceinline__ uint32_t vword(const uint4 &v, uint32_t j) {
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set_vword(uint4 &v, uint32_t j, uint32_t w) {
+    if (j == 0) v.x = w;
+    else if (j == 1) v.y = w;
+    else if (j == 2) v.z = w;
+    else v.w = w;
 }
 
 __device__ __forceinline__ bool is_neg(float a) { return a < 0.0f; }
@@ -360,16 +413,10 @@ __device__ __forceinline__ float4 fg4(float4 a, float4 b, uint32_t bits) {
 template <uint32_t KIND>
 __device__ __forceinline__ uint4 fg4(uint4 a, uint4 b, uint32_t bits) {
     uint4 r;
-    if (KIND == OP_F) {
-        r.x = f_i8x4(a.x, b.x); r.y = f_i8x4(a.y, b.y); r.z = f_i8x4(a.z, b.z); r.w = f_i8x4(a.w, b.w);
-    } else if (KIND == OP_G) {
-        r.x = g_i8x4(a.x, b.x, bits & 0xFu);
-        r.y = g_i8x4(a.y, b.y, (bits >> 4) & 0xFu);
-        r.z = g_i8x4(a.z, b.z, (bits >> 8) & 0xFu);
-        r.w = g_i8x4(a.w, b.w, (bits >> 12) & 0xFu);
-    } else {
-        r.x = g0r_i8x4(a.x, b.x); r.y = g0r_i8x4(a.y, b.y); r.z = g0r_i8x4(a.z, b.z); r.w = g0r_i8x4(a.w, b.w);
-    }
+    r.x = op_i8x4<KIND>(a.x, b.x, bits & 0xFu);
+    r.y = op_i8x4<KIND>(a.y, b.y, (bits >> 4) & 0xFu);
+    r.z = op_i8x4<KIND>(a.z, b.z, (bits >> 8) & 0xFu);
+    r.w = op_i8x4<KIND>(a.w, b.w, (bits >> 12) & 0xFu);
     return r;
 }
 
@@ -450,20 +497,54 @@ __device__ __forceinline__ void op_chain(const T *__restrict__ in, T *__restrict
         Vec x[M];
 #pragma unroll
         for (uint32_t m = 0; m < M; ++m) x[m] = ldv<RD>(vi + c + m * nvc, pol);
-        Vec y[M / 2];
+        if constexpr (sizeof(T) == 1) {
+            // int8: word by word in f16 pairs; intermediate stages are packed
+            // back to bytes only where they are stored
+            uint32_t gb[M / 2];
 #pragma unroll
-        for (uint32_t m = 0; m < M / 2; ++m) {
-            const uint32_t bits = K0 == OP_G ? bits_at(beta, o + (c + m * nvc) * V, V) : 0u;
-            y[m] = fg4<K0>(x[m], x[m + M / 2], bits);
-            if (STORE & 1u) v1[c + m * nvc] = y[m];
-        }
-        Vec z[M / 4];
+            for (uint32_t m = 0; m < M / 2; ++m)
+                gb[m] = K0 == OP_G ? bits_at(beta, o + (c + m * nvc) * V, V) : 0u;
+            Vec y[M / 2], z[M / 4], w;
 #pragma unroll
-        for (uint32_t m = 0; m < M / 4; ++m) {
-            z[m] = fg4<K1>(y[m], y[m + M / 4], 0u);
-            if (L == 2 || (STORE & 2u)) v2[c + m * nvc] = z[m];
+            for (uint32_t j = 0; j < 4; ++j) {
+                H4 xh[M], yh[M / 2], zh[M / 4];
+#pragma unroll
+                for (uint32_t m = 0; m < M; ++m) xh[m] = h4_unpack(vword(x[m], j));
+#pragma unroll
+                for (uint32_t m = 0; m < M / 2; ++m) {
+                    yh[m] = h4_op<K0>(xh[m], xh[m + M / 2], (gb[m] >> (4 * j)) & 0xFu);
+                    if (STORE & 1u) set_vword(y[m], j, h4_pack(yh[m]));
+                }
+#pragma unroll
+                for (uint32_t m = 0; m < M / 4; ++m) {
+                    zh[m] = h4_op<K1>(yh[m], yh[m + M / 4], 0u);
+                    if (L == 2 || (STORE & 2u)) set_vword(z[m], j, h4_pack(zh[m]));
+                }
+                if constexpr (L == 3) set_vword(w, j, h4_pack(h4_op<K2>(zh[0], zh[1], 0u)));
+            }
+#pragma unroll
+            for (uint32_t m = 0; m < M / 2; ++m)
+                if (STORE & 1u) v1[c + m * nvc] = y[m];
+#pragma unroll
+            for (uint32_t m = 0; m < M / 4; ++m)
+                if (L == 2 || (STORE & 2u)) v2[c + m * nvc] = z[m];
+            if constexpr (L == 3) v3[c] = w;
+        } else {
+            Vec y[M / 2];
+#pragma unroll
+            for (uint32_t m = 0; m < M / 2; ++m) {
+                const uint32_t bits = K0 == OP_G ? bits_at(beta, o + (c + m * nvc) * V, V) : 0u;
+                y[m] = fg4<K0>(x[m], x[m + M / 2], bits);
+                if (STORE & 1u) v1[c + m * nvc] = y[m];
+            }
+            Vec z[M / 4];
+#pragma unroll
+            for (uint32_t m = 0; m < M / 4; ++m) {
+                z[m] = fg4<K1>(y[m], y[m + M / 4], 0u);
+                if (L == 2 || (STORE & 2u)) v2[c + m * nvc] = z[m];
+            }
+            if constexpr (L == 3) v3[c] = fg4<K2>(z[0], z[1], 0u);
         }
-        if constexpr (L == 3) v3[c] = fg4<K2>(z[0], z[1], 0u);
     }
 }
 
