@@ -453,9 +453,10 @@ void emit_body(std::ostringstream &o, const polar_code &code, bool is_i8, uint32
     // operation of the node it produced LLRs for: F or G_0R): emitted as one
     // fused op_chain when the last stage holds at least one vector per column.
     // Returns the number of operations covered (1 = not fused). int8 chains stop
-    // at two operations: three hold 56 registers of 16-byte vectors and measured
-    // slower under the 72-register budget of the int8 decoder (more local
-    // memory); float32 chains go to three.
+    // at two operations: three hold eight 16-byte input vectors, which under the
+    // 72-register budget of the int8 decoder means more local memory, and they
+    // measured slower (with byte-wise and with f16 arithmetic alike); float32
+    // chains go to three.
     const uint32_t vec = is_i8 ? 16u : 4u;
     const uint32_t max_chain = is_i8 ? 2u : 3u;
     auto chain_len = [&](size_t i) -> uint32_t {

@@ -14,8 +14,10 @@
 // [off, off+n), Combine rewrites only the left half), bit-packed in shared
 // memory. float32: F is an exact min with the XOR of the sign bits (beta in
 // {+0,-0}), G adds alpha_v[i] with its sign flipped by beta_l (Listing 3): one
-// IEEE add. int8: G is a saturating add followed by max(-127) (Listing 4).
-// Every operation agrees bit for bit with a scalar evaluation in the same order.
+// IEEE add. int8: G is a saturating add followed by max(-127) (Listing 4);
+// in memory-level operations the int8 values are computed as f16 pairs, which
+// is exact for them (see op_i8x4). Every operation agrees bit for bit with a
+// scalar evaluation in the same order.
 #pragma once
 
 #ifdef __CUDACC_RTC__
