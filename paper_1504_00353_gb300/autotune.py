@@ -289,6 +289,10 @@ class CodeTuner:
             cur, _ = self.best(T)
             # the inlined decoder against one with shared code for equal subtrees
             self.measure([dict(cur, compile_form=f) for f in ("auto", "subtrees")])
+            cur, _ = self.best(T)
+            # register-resident subtree size: the depth below which a frame's
+            # tree is decoded in registers instead of through memory stages
+            self.measure([dict(cur, reg_subtree=r) for r in (256, 512)])
         return self.best(T)
 
 

@@ -65,3 +65,33 @@ def test_module_entry_point_defines_everything_it_uses():
     last = tree.body[-1]
     assert isinstance(last, ast.If) and "__main__" in ast.dump(last.test)
     assert autotune.SHAPE_DEFAULTS["compile_form"] in autotune.COMPILE_FORM
+
+
+def test_throughput_search_reaches_form_and_register_subtree():
+    """The coordinate search (threads, stage cap, warp threshold, resident CTAs,
+    frames per CTA, compile form, register-subtree size) run against a synthetic
+    cost table with no GPU: it must end at the cheapest shape when each knob's
+    best value can be found one coordinate at a time."""
+    class FakeTuner(autotune.CodeTuner):
+        def __init__(self):  # no device: only the search logic
+            self.N, self.K, self.dtype, self.latency = 32768, 29492, "i8", False
+            self.seen, self.log, self.asked = {}, None, []
+
+        def measure(self, shapes):
+            for s in map(self.clamp, shapes):
+                self.asked.append(s)
+                t = 10.0
+                t -= {32: 2.0, 64: 1.0}.get(s["threads"], 0.0)
+                t -= {1024: 1.0}.get(s["smem_stage_max"], 0.0)
+                t -= {4: 1.5, 2: 0.5}.get(s["frames_per_cta"], 0.0)
+                t -= 0.8 if s["compile_form"] == "subtrees" else 0.0
+                t -= 0.4 if s["reg_subtree"] == 512 else 0.0
+                self.seen[autotune._shape_key(s)] = t
+
+    t = FakeTuner()
+    best, cost = t.tune()
+    assert best["threads"] == 32 and best["frames_per_cta"] == 4
+    assert best["smem_stage_max"] == 1024
+    assert best["compile_form"] == "subtrees" and best["reg_subtree"] == 512
+    assert cost == min(t.seen.values())
+    assert any(s["reg_subtree"] == 512 for s in t.asked)
